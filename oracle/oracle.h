@@ -1,0 +1,157 @@
+/*
+ * oracle.h -- plain FP64 CPU oracle for athermal quasistatic (AQS) deformation
+ * stepping and its two-level parallel scheme (Reihn, Bamer, Stamm,
+ * "Parallel athermal quasistatic deformation stepping of molecular systems").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code is the slow, obviously correct
+ * definition that the CUDA library is checked against.  Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark may load it; the
+ * product path never calls it and shares no code with it.
+ *
+ * Everything is FP64, O(N^2) all-pairs, single pass over plain arrays.
+ * Conventions (shared with the library by specification, not by code):
+ *   - dim d in {2,3}; positions are N x d, row-major, Cartesian.
+ *   - the cell is H (d x d, row-major), upper triangular; its columns are the
+ *     Bravais vectors (Sec. 2.1).  Simple shear only tilts H[0][1] (Eq. 16).
+ *   - minimum image: subtract lattice vectors from the last axis to the
+ *     first (z, then y, then x), each by rounding the fractional coordinate
+ *     of that axis (reading of the periodic boundaries of Sec. 2.1 for a
+ *     sheared cell; valid while the cutoff is below half of every
+ *     perpendicular cell width).
+ *
+ * Readings where the paper is silent are stated next to each function.
+ * Functions whose result has no independent pin say "parity unpinned".
+ */
+#ifndef AQS_ORACLE_H
+#define AQS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAX_TYPES 4
+
+/* status codes (same numbering as the library's, fixed by specification) */
+enum {
+  ORC_OK = 0,
+  ORC_ERR_INVALID_ARG = 1,
+  ORC_ERR_NOT_CONVERGED = 4,
+  ORC_ERR_NONFINITE = 5,
+  ORC_ERR_BOX_TOO_SMALL = 7
+};
+
+/* Binary Lennard-Jones model (Sec. 2.2, Eq. 13) with a shifted-force cutoff
+ * rc_ab = rc_factor * sigma_ab.  sigma/eps are n_types x n_types row-major and
+ * symmetric. */
+typedef struct {
+  int dim;
+  int n_types;
+  double sigma[ORC_MAX_TYPES * ORC_MAX_TYPES];
+  double eps[ORC_MAX_TYPES * ORC_MAX_TYPES];
+  double rc_factor;
+} orc_potential;
+
+/* FIRE parameters.  The paper minimises with conjugate gradients (Sec. 2.1);
+ * the accelerated path uses FIRE, written out in orc_fire(). */
+typedef struct {
+  double dt0, alpha0, f_inc, f_dec, f_alpha, dt_max, dt_min, max_step, tol;
+  int n_min;
+  int64_t max_iter;
+} orc_fire_params;
+
+/* ---- geometry (Sec. 2.1) ---- */
+double orc_volume(int dim, const double* H);
+/* in-place minimum image of a separation vector d (length dim) */
+void orc_min_image(int dim, const double* H, double* d);
+/* largest cutoff allowed by the minimum-image rule: half the smallest
+ * perpendicular width of the cell */
+double orc_half_min_width(int dim, const double* H);
+/* simple-shear affine map F^(dgamma) (Eq. 16): r_i <- F r_i for all atoms
+ * (Eq. 3) and H <- F H (Eq. 1) */
+void orc_affine_shear(int dim, int n, double* x, double* H, double dgamma);
+/* general affine map with a d x d matrix F (row-major): r_i <- F r_i, H <- F H */
+void orc_affine_map(int dim, int n, double* x, double* H, const double* F);
+
+/* ---- energy model (Sec. 2.1 Eqs. 4-6, Sec. 2.2 Eq. 13) ---- */
+/* shifted-force LJ pair: for squared distance s returns U_sf(r) and U_sf'(r)
+ * (derivative w.r.t. r); zero beyond rc */
+void orc_pair_sflj(double s, double sigma, double eps, double rc, double* u, double* du);
+/* all-pairs energy E = sum_{i<j} U_sf(r_ij), forces F = -grad E (N x d,
+ * nullable) and shear stress tau = (1/V) dE/dgamma (nullable) */
+int orc_energy_forces(const orc_potential* pot, int n, const double* x, const int32_t* types,
+                      const double* H, double* E, double* F, double* tau);
+double orc_fmax(int dim, int n, const double* F);
+
+/* ---- minimiser F of Eq. 10 ---- */
+/* FIRE from x (in/out).  Optional traces (length trace_cap, nullable): energy
+ * at every force evaluation and a flag that is 1 where the velocity was reset.
+ * Returns status; *iters = number of position updates made. */
+int orc_fire(const orc_potential* pot, const orc_fire_params* fp, int n, double* x,
+             const int32_t* types, const double* H, int64_t* iters, double* E, double* fmax,
+             double* e_trace, uint8_t* reset_trace, int64_t trace_cap);
+/* Polak-Ribiere conjugate gradients with Armijo backtracking (monotone by
+ * construction); the paper's own choice of minimiser (Sec. 2.1). */
+int orc_cg(const orc_potential* pot, int n, double* x, const int32_t* types, const double* H,
+           double tol, int64_t max_iter, int64_t* iters, double* E, double* fmax,
+           double* e_trace, int64_t trace_cap);
+
+/* ---- equality and non-affine displacement ---- */
+/* max over atoms of | mi(a_i - b_i) - mean_j mi(a_j - b_j) |  (both at the
+ * same H); used for the basin test (Eq. 20) and the per-step non-affine
+ * displacement D_k */
+double orc_max_rel_disp(int dim, int n, const double* a, const double* b, const double* H);
+
+/* ---- AQS protocol (Eq. 12) ---- */
+/* n_steps sequential steps of r <- F(F_N^(dgamma) r).  x, H in/out.  Per-step
+ * outputs (length n_steps, each nullable): energy E_k, stress tau_k, FIRE
+ * iterations, non-affine displacement D_k. */
+int orc_aqs(const orc_potential* pot, const orc_fire_params* fp, int n, double* x,
+            const int32_t* types, double* H, double dgamma, int n_steps, double* E_k,
+            double* tau_k, int64_t* iters_k, double* D_k);
+
+/* ---- two-level parallel stepping (Sec. 3, Algorithm 1) ---- */
+typedef struct {
+  int64_t iterations;       /* passes of the while loop */
+  int64_t fire_iters_total; /* FIRE iterations of all chains, rejected ones included */
+  int64_t n_log;            /* entries written to the decision log */
+} orc_parallel_stats;
+
+/* Runs Algorithm 1 from the minimum x (in/out, becomes r_{N_steps}).
+ * Per accepted step k (length n_steps, nullable): E_k, tau_k, iters_k, D_k.
+ * Decision log (capacity log_cap, nullable): for every equality test made,
+ * log_iter = while-loop pass, log_i = chain index i, log_eq = 1 if equal,
+ * log_m = measured max displacement.  n_threads > 1 runs the level-II
+ * chains on that many POSIX threads (the paper's design). */
+int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, double* x,
+                 const int32_t* types, double* H, double dgamma, int K, int P, int n_steps,
+                 double eq_tol, int n_threads, double* E_k, double* tau_k, int64_t* iters_k,
+                 double* D_k, int64_t* log_iter, int32_t* log_i, uint8_t* log_eq, double* log_m,
+                 int64_t log_cap, orc_parallel_stats* stats);
+
+/* Pure decision rule of Algorithm 1 (lines after the level-II loop): given
+ * the chain lengths K_i (i = 0..P_eff-1) and the equality outcomes eq[i] for
+ * i = 1..P_eff-1, returns q (accepted fine steps) and *first_fail (-1 if none). */
+int64_t orc_alg1_decide(int P_eff, const int32_t* K_i, const uint8_t* eq, int32_t* first_fail);
+
+/* ---- learned warm start: per-atom features and FP64 MLP ---- */
+/* Features of atom i: min-image displacements to its n_nb nearest atoms
+ * (ascending distance, ties by index), followed by a one-hot species code of
+ * width n_types.  Output n x (n_nb*dim + n_types), row-major. */
+int orc_knn_features(int dim, int n, const double* x, const int32_t* types, const double* H,
+                     int n_types, int n_nb, double* feat);
+/* MLP with GELU hidden layers: layer l maps width[l] -> width[l+1];
+ * weights W_l are width[l+1] x width[l] row-major, biases b_l.
+ * Forward on m rows of X (m x width[0]); Y is m x width[L]. */
+int orc_mlp_forward(int n_layers, const int32_t* width, const double* const* W,
+                    const double* const* b, int64_t m, const double* X, double* Y);
+/* Mean-squared-error loss 0.5/m * sum (Y - T)^2 and its gradients w.r.t. all
+ * weights and biases (dW, db laid out like W, b). */
+double orc_mlp_loss_grad(int n_layers, const int32_t* width, const double* const* W,
+                         const double* const* b, int64_t m, const double* X, const double* T,
+                         double* const* dW, double* const* db);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
