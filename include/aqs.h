@@ -1,0 +1,237 @@
+/*
+ * aqs.h -- C ABI of the GB300 (sm_103a) library for athermal quasistatic (AQS)
+ * deformation stepping and its two-level parallel scheme
+ * (Reihn, Bamer, Stamm, "Parallel athermal quasistatic deformation stepping
+ * of molecular systems").
+ *
+ * The library holds one or more "replicas" (independent particle systems of
+ * the same dimension and potential) on one GPU and runs, per replica:
+ *   - the affine deformation F^(dgamma) of the cell and of every atom
+ *     (Sec. 2.1, Eqs. 1-3; simple shear, Eq. 16);
+ *   - the minimisation operator F: r -> r_inf (Sec. 2.1, Eq. 10), here FIRE
+ *     with shifted-force Lennard-Jones forces (Sec. 2.2, Eq. 13) from cell
+ *     and Verlet lists under Lees-Edwards periodic boundaries;
+ *   - sequential AQS (Eq. 12) and the two-level parallel stepping of Sec. 3
+ *     (Algorithm 1) with the equality test of Eq. 20.
+ *
+ * Conventions
+ *   - dim d in {2, 3}.  Positions are N x d row-major Cartesian, in the
+ *     caller's atom order ("user order"); the library reorders atoms
+ *     internally and always converts back.
+ *   - The cell H is d x d row-major, upper triangular; its columns are the
+ *     Bravais vectors.  Simple shear adds dgamma * H[1][1] to H[0][1] and
+ *     dgamma * y to every x.  The tilt must stay within the minimum-image
+ *     rule: cutoff + skin below half of every perpendicular cell width.
+ *   - Positions returned by the library may differ from the ones passed in
+ *     by whole lattice vectors (atoms are wrapped into the cell when the
+ *     neighbour lists are rebuilt); compare configurations by minimum image.
+ *   - Pointers marked "host or device" are classified with
+ *     cudaPointerGetAttributes; device pointers must be on the library's GPU.
+ *
+ * Errors: every call returns an aqs_status; no call aborts or throws.  The
+ * thread-local text of the last error is available from aqs_last_error().
+ * Device code never traps: kernels write a status word that the host reads.
+ *
+ * Threading: one system is used from one host thread at a time; all work of
+ * a system is ordered on the stream given at creation.
+ */
+#ifndef AQS_H
+#define AQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AQS_MAX_TYPES 4
+
+typedef enum {
+  AQS_OK = 0,
+  AQS_ERR_INVALID_ARG = 1,
+  AQS_ERR_CUDA = 2,
+  AQS_ERR_OOM = 3,
+  AQS_ERR_NOT_CONVERGED = 4,  /* FIRE hit max_iter */
+  AQS_ERR_NONFINITE = 5,      /* NaN/Inf force or energy */
+  AQS_ERR_NLIST_OVERFLOW = 6, /* internal; the library grows the list and retries */
+  AQS_ERR_BOX_TOO_SMALL = 7,  /* cutoff + skin >= half a perpendicular cell width */
+  AQS_ERR_TIMEOUT = 8,
+  AQS_ERR_UNSUPPORTED = 9
+} aqs_status;
+
+typedef enum {
+  AQS_FP64 = 0,  /* every force evaluation in FP64 */
+  AQS_MIXED = 1  /* FP32 pair forces relative to an FP64 reference force; FP64
+                    positions, reductions and final convergence test */
+} aqs_precision;
+
+/* Binary (up to 4 species) Lennard-Jones model, Sec. 2.2 Eq. 13, with the
+ * shifted-force cutoff rc_ab = rc_factor * sigma_ab:
+ *   U_sf(r) = U(r) - U(rc) - (r - rc) U'(rc) for r < rc, 0 beyond.
+ * sigma, eps: n_types x n_types row-major, symmetric. */
+typedef struct {
+  int n_types;
+  double sigma[AQS_MAX_TYPES * AQS_MAX_TYPES];
+  double eps[AQS_MAX_TYPES * AQS_MAX_TYPES];
+  double rc_factor;
+} aqs_potential;
+
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int n_replicas;          /* >= 1 */
+  const int64_t* n_atoms;  /* host [n_replicas]; each >= 2 */
+  const double* box;       /* host [n_replicas * dim * dim], H per replica */
+  const double* pos;       /* host or device [sum n_atoms * dim], user order */
+  const int32_t* types;    /* host or device [sum n_atoms], values < n_types */
+  aqs_potential pot;
+  aqs_precision precision;
+  double skin;             /* Verlet skin; <= 0 selects 0.3 */
+  int nlist_capacity;      /* neighbours per atom; <= 0 selects 64 (2D) / 160 (3D) */
+  int cluster_size;        /* CTAs per replica (1..16); <= 0 selects automatically */
+  void* stream;            /* cudaStream_t for all work; NULL = legacy default stream */
+  /* optional device allocator (e.g. a framework's caching allocator); both
+   * NULL selects cudaMalloc/cudaFree.  The library never frees what it did
+   * not allocate. */
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+} aqs_system_desc;
+
+typedef struct aqs_system aqs_system; /* opaque; owns all device state */
+
+/* FIRE controls (the minimiser F of Eq. 10).  The library's FIRE:
+ *   P = F.v; P >= 0: npos++, after n_min such steps dt = min(dt*f_inc, dt_max),
+ *   alpha *= f_alpha; P < 0: npos = 0, dt = max(dt*f_dec, dt_min),
+ *   alpha = alpha0, v = 0; then v += dt F, v = (1-alpha) v + alpha |v|/|F| F,
+ *   per-atom step dt v capped at max_step.  Converged when max_a |F_a| < tol
+ *   (tested before moving; in AQS_MIXED always on an FP64 evaluation).
+ * ref_ratio / ref_dmax (AQS_MIXED only): a new FP64 reference force is taken
+ * when an atom has moved more than min(ref_ratio * fmax, ref_dmax) from the
+ * reference positions. */
+typedef struct {
+  double dt0, alpha0, f_inc, f_dec, f_alpha, dt_max, dt_min, max_step, tol;
+  int n_min;
+  int64_t max_iter;
+  double ref_ratio, ref_dmax;
+} aqs_fire_params;
+
+/* dt0 0.005, alpha0 0.1, f_inc 1.1, f_dec 0.5, f_alpha 0.99, dt_max 0.05,
+ * dt_min 1e-4, max_step 0.1, tol 1e-10, n_min 5, max_iter 1e6,
+ * ref_ratio 30, ref_dmax 0.05 */
+void aqs_fire_params_default(aqs_fire_params* out);
+
+typedef struct {
+  int64_t iters;     /* FIRE position updates */
+  int64_t evals64;   /* FP64 force evaluations (every evaluation in AQS_FP64) */
+  int64_t rebuilds;  /* neighbour-list rebuilds during the call */
+  double energy;     /* U at the minimum (FP64) */
+  double fmax;       /* max_a |F_a| at the minimum (FP64) */
+  double tau;        /* shear stress (1/V) dU/dgamma at the minimum */
+  double nonaffine;  /* max_a |(r_a - r_a^start) - mean| over the call */
+  int status;        /* aqs_status of this replica */
+} aqs_min_result;
+
+/* Creates a system; copies pos/types.  Fails with AQS_ERR_BOX_TOO_SMALL when
+ * the cell is too small for the cutoff and skin. */
+aqs_status aqs_create_system(const aqs_system_desc* desc, aqs_system** out);
+void aqs_destroy_system(aqs_system* sys);
+
+/* Simple shear F^(dgamma) (Eq. 16) of every atom and of the cell of each
+ * replica; dgamma: host [n_replicas] (a replica with 0 is untouched). */
+aqs_status aqs_affine_shear(aqs_system* sys, const double* dgamma);
+
+/* Minimisation operator F (Eq. 10) on all replicas with mask[r] != 0
+ * (mask NULL = all), batched in one persistent launch per pass.
+ * out: host [n_replicas] (entries of masked-out replicas untouched);
+ * returns the first non-OK replica status, else AQS_OK. */
+aqs_status aqs_minimize(aqs_system* sys, const aqs_fire_params* fire, const uint8_t* mask,
+                        aqs_min_result* out);
+
+/* Sequential AQS (Eq. 12) on every replica at once: n_steps times
+ * [affine dgamma; minimise].  Per-step outputs, host, [n_steps * n_replicas]
+ * step-major (nullable each): energy, tau, FIRE iterations, non-affine
+ * displacement D_k = max_a |mi(r_k,a - (F r_{k-1})_a) - mean|. */
+aqs_status aqs_run_sequential(aqs_system* sys, const aqs_fire_params* fire, double dgamma,
+                              int64_t n_steps, double* energy, double* tau, int64_t* fire_iters,
+                              double* nonaffine);
+
+/* Two-level parallel stepping, Algorithm 1 (Sec. 3.5), from the minimum held
+ * in `replica` (r_star).  Level I makes P affine predictions
+ * F^(i K dgamma) r_star (Eq. 18); level II runs the P chains
+ * (F o F_N)^K o F (Eq. 19) as replicas of one batched launch; the equality
+ * test (Eq. 20) compares, for i = 1..P-1, the end of chain i-1 with F(r^c_iK)
+ * by max_a |mi(a - b) - mean| < eq_tol; r_star <- r_q.
+ * Readings: the last window runs P_eff = min(P, ceil(rem/K)) chains, the last
+ * one shortened to end exactly at n_steps; a step is a plastic event when its
+ * D_k exceeds event_threshold. */
+typedef struct {
+  double dgamma;          /* fine increment */
+  int K;                  /* fine steps per chain (>= 1) */
+  int P;                  /* chains (>= 1) */
+  int64_t n_steps;        /* fine steps to advance in this call */
+  double eq_tol;          /* <= 0 selects 1e-6 */
+  double event_threshold; /* <= 0 selects 1e-2 */
+  int64_t max_iterations; /* while-loop passes in this call; <= 0: until n_steps */
+  int warm_start;         /* 1: start each fine minimisation from the learned
+                             prediction (see aqs_warm_*); 0: plain affine start */
+} aqs_parallel_params;
+
+typedef struct {
+  int64_t iterations;       /* while-loop passes made */
+  int64_t accepted_steps;   /* fine steps accepted (= advance of r_star) */
+  int64_t rejections;       /* passes that ended at a failed equality test */
+  int64_t fire_iters_total; /* FIRE iterations of all chains, rejected ones included */
+  int64_t evals64_total;    /* FP64 force evaluations of all chains */
+  /* caller-allocated host arrays indexed by accepted step (nullable each),
+   * capacity n_steps: */
+  double* energy;
+  double* tau;
+  int64_t* fire_iters;
+  double* nonaffine;
+  uint8_t* event;
+  /* decision log, caller-allocated, capacity log_cap: one entry per equality
+   * test made (pass, chain index i, equal?, measured displacement) */
+  int64_t log_cap;
+  int64_t n_log;
+  int64_t* log_iter;
+  int32_t* log_i;
+  uint8_t* log_eq;
+  double* log_m;
+} aqs_parallel_result;
+
+aqs_status aqs_parallel_step(aqs_system* sys, int replica, const aqs_fire_params* fire,
+                             const aqs_parallel_params* params, aqs_parallel_result* out);
+
+/* Equality test of Eq. 20 between replica ra of a and replica rb of b (same
+ * atom count, same cell): max_disp = max_a |mi(r_a - r_b) - mean|,
+ * equal = max_disp < tol.  The two systems must share one stream. */
+aqs_status aqs_compare_configs(const aqs_system* a, int ra, const aqs_system* b, int rb,
+                               double tol, double* max_disp, int* equal);
+
+/* ---- state access ---- */
+int aqs_num_replicas(const aqs_system* sys);
+int64_t aqs_num_atoms(const aqs_system* sys, int replica);
+/* out: host or device [n * dim], user order */
+aqs_status aqs_get_positions(const aqs_system* sys, int replica, double* out);
+/* pos: host or device [n * dim], user order; resets FIRE state of the replica */
+aqs_status aqs_set_positions(aqs_system* sys, int replica, const double* pos);
+aqs_status aqs_get_box(const aqs_system* sys, int replica, double* H);
+aqs_status aqs_set_box(aqs_system* sys, int replica, const double* H);
+/* FP64 energy, forces (host or device [n * dim], user order, nullable) and
+ * shear stress (nullable) of one replica at its current positions */
+aqs_status aqs_energy_forces(aqs_system* sys, int replica, double* energy, double* forces,
+                             double* tau);
+
+/* ---- diagnostics ---- */
+const char* aqs_last_error(void);
+/* number of kernels this library launched in this process */
+int64_t aqs_launch_count(void);
+/* mean neighbour-list length of a replica after the last rebuild */
+double aqs_mean_neighbours(const aqs_system* sys, int replica);
+int aqs_cluster_size(const aqs_system* sys, int replica);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AQS_H */

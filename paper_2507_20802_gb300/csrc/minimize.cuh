@@ -1,0 +1,32 @@
+// minimize.cuh -- arguments and launcher of the persistent FIRE minimiser.
+#pragma once
+#include "aqs_internal.cuh"
+
+namespace aqs {
+
+struct MinArgs {
+  const RepGeom* geom;
+  RepState* state;
+  const int* work;  // replica index per cluster
+  double* x;        // [D][ntot]; holds x_ref inside a launch in mixed mode
+  double* v;        // [D][ntot]
+  double* fref;     // [D][ntot] (mixed)
+  double* dl;       // [D][ntot] delta (mixed)
+  double* xs;       // [D][ntot] positions at the start of the minimisation
+  const double* xb; // [D][ntot] positions at the last list build (affinely mapped)
+  const int32_t* type;
+  const int32_t* cell;
+  const uint32_t* nb;
+  const int32_t* nnb;
+  const PairCoef* coef;
+  int64_t ntot;
+  int nt;
+  FireDev fire;
+  double skin, rlist;
+};
+
+size_t minimize_smem_bytes(int dim, int npc, int nt);
+cudaError_t launch_minimize(int dim, bool mixed, const MinArgs& a, int n_clusters, int C, int npc,
+                            cudaStream_t s);
+
+}  // namespace aqs

@@ -1,0 +1,1150 @@
+// runtime.cu -- host runtime and C ABI (include/aqs.h): system state on the
+// device, list rebuilds, the batched minimiser driver, sequential AQS and the
+// two-level parallel stepping of Sec. 3 (Algorithm 1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "aqs_internal.cuh"
+#include "launch.cuh"
+#include "lists.cuh"
+#include "minimize.cuh"
+#include "misc.cuh"
+
+namespace aqs {
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local std::string g_err;
+
+static aqs_status fail(aqs_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+}  // namespace aqs
+
+using namespace aqs;
+
+#define CUDA_TRY(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(AQS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define AQS_TRY(call)                      \
+  do {                                     \
+    aqs_status s_ = (call);                \
+    if (s_ != AQS_OK) return s_;           \
+  } while (0)
+
+struct Alloc {
+  void* p;
+  size_t bytes;
+};
+
+struct aqs_system {
+  int dim = 2, R = 0, nt = 0, prec = 0, cap = 0, C_override = 0;
+  aqs_potential pot{};
+  double skin = 0.3, rcmax = 0.0, rlist = 0.0;
+  cudaStream_t stream = nullptr;
+  void* (*ualloc)(size_t, void*) = nullptr;
+  void (*ufree)(void*, void*) = nullptr;
+  void* actx = nullptr;
+  std::vector<int64_t> n, off;
+  int64_t ntot = 0, nmax = 0;
+  std::vector<RepGeom> geom;
+  std::vector<RepState> st;
+  std::vector<double> mean_nb;
+  PairCoef coef[AQS_MAX_TYPES * AQS_MAX_TYPES];
+  float rl2f[AQS_MAX_TYPES * AQS_MAX_TYPES];
+  int total_cells = 0, cells_cap = 0;
+  std::vector<Alloc> allocs;
+  // device arrays
+  RepGeom* d_geom = nullptr;
+  RepState* d_state = nullptr;
+  PairCoef* d_coef = nullptr;
+  int* d_work = nullptr;
+  uint8_t* d_flag = nullptr;
+  int32_t* d_rep_of = nullptr;
+  double *x = nullptr, *v = nullptr, *fref = nullptr, *dl = nullptr, *xs = nullptr, *xb = nullptr;
+  double *tmp = nullptr, *d_dg = nullptr, *ubuf = nullptr, *ubuf2 = nullptr;
+  int32_t *type = nullptr, *perm = nullptr, *inv = nullptr, *cell = nullptr, *key = nullptr;
+  int32_t *itmp = nullptr, *nnb = nullptr, *count = nullptr, *cstart = nullptr, *cell_rep = nullptr;
+  int32_t* overflow = nullptr;
+  int64_t* order = nullptr;
+  uint32_t* nb = nullptr;
+  size_t nb_bytes = 0;
+  CmpJob* d_jobs = nullptr;
+  double* d_cmp = nullptr;
+  double* d_partial = nullptr;
+  int64_t* d_i64 = nullptr;  // small scratch (copy offsets)
+  double* d_shift = nullptr;
+  // two-level stepping resources
+  aqs_system* chains = nullptr;
+  double* snap = nullptr;
+  double* ends = nullptr;
+};
+
+namespace {
+
+void* dalloc(aqs_system* s, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (s->ualloc) {
+    p = s->ualloc(bytes, s->actx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) s->allocs.push_back({p, bytes});
+  return p;
+}
+
+void dfree(aqs_system* s, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < s->allocs.size(); i++)
+    if (s->allocs[i].p == p) {
+      if (s->ufree) s->ufree(p, s->actx);
+      else cudaFree(p);
+      s->allocs.erase(s->allocs.begin() + i);
+      return;
+    }
+}
+
+template <typename T>
+aqs_status alloc_arr(aqs_system* s, T** p, size_t count) {
+  *p = static_cast<T*>(dalloc(s, count * sizeof(T)));
+  if (!*p) return fail(AQS_ERR_OOM, "device allocation of %zu bytes failed", count * sizeof(T));
+  return AQS_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+double lj_u(double r, double sig, double eps) {
+  double sr = sig / r, sr2 = sr * sr, sr6 = sr2 * sr2 * sr2;
+  return 4.0 * eps * (sr6 * sr6 - sr6);
+}
+double lj_du(double r, double sig, double eps) {
+  double sr = sig / r, sr2 = sr * sr, sr6 = sr2 * sr2 * sr2;
+  return -24.0 * eps * (2.0 * sr6 * sr6 - sr6) / r;
+}
+
+// perpendicular widths of an upper-triangular cell whose only tilt is H[0][1]
+void cell_widths(int D, const double* H, double* w) {
+  double Ly = H[1 * D + 1], t = H[0 * D + 1];
+  w[0] = H[0] / std::sqrt(1.0 + (t / Ly) * (t / Ly));
+  w[1] = Ly;
+  if (D == 3) w[2] = H[8];
+}
+
+int auto_cluster(int R, int64_t n) {
+  int C = std::max(1, 152 / std::max(1, R));
+  C = std::min(C, kMaxCluster);
+  C = (int)std::min<int64_t>(C, std::max<int64_t>(1, n / 32));
+  while ((n + C - 1) / C > 4096 && C < kMaxCluster) C++;
+  return C;
+}
+
+aqs_status upload_geom(aqs_system* s) {
+  CUDA_TRY(cudaMemcpyAsync(s->d_geom, s->geom.data(), sizeof(RepGeom) * s->R,
+                           cudaMemcpyHostToDevice, s->stream));
+  return AQS_OK;
+}
+
+aqs_status upload_state(aqs_system* s) {
+  CUDA_TRY(cudaMemcpyAsync(s->d_state, s->st.data(), sizeof(RepState) * s->R,
+                           cudaMemcpyHostToDevice, s->stream));
+  return AQS_OK;
+}
+
+aqs_status download_state(aqs_system* s) {
+  CUDA_TRY(cudaMemcpyAsync(s->st.data(), s->d_state, sizeof(RepState) * s->R,
+                           cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return AQS_OK;
+}
+
+BuildArgs build_args(aqs_system* s) {
+  BuildArgs a;
+  a.geom = s->d_geom;
+  a.rep_of = s->d_rep_of;
+  a.flag = s->d_flag;
+  a.x = s->x;
+  a.v = s->v;
+  a.xs = s->xs;
+  a.xb = s->xb;
+  a.type = s->type;
+  a.perm = s->perm;
+  a.inv = s->inv;
+  a.cell = s->cell;
+  a.key = s->key;
+  a.order = s->order;
+  a.count = s->count;
+  a.cstart = s->cstart;
+  a.cell_rep = s->cell_rep;
+  a.tmp = s->tmp;
+  a.itmp = s->itmp;
+  a.nb = s->nb;
+  a.nnb = s->nnb;
+  a.overflow = s->overflow;
+  for (int k = 0; k < AQS_MAX_TYPES * AQS_MAX_TYPES; k++) a.rl2f[k] = s->rl2f[k];
+  a.nt = s->nt;
+  a.cap = s->cap;
+  a.ntot = s->ntot;
+  return a;
+}
+
+aqs_status layout_lists(aqs_system* s) {
+  int64_t total = 0;
+  for (int r = 0; r < s->R; r++) {
+    s->geom[r].nb_off = total;
+    total += (int64_t)s->cap * s->n[r];
+  }
+  if (s->nb) dfree(s, s->nb);
+  s->nb = nullptr;
+  s->nb_bytes = sizeof(uint32_t) * (size_t)total;
+  return alloc_arr(s, &s->nb, (size_t)total);
+}
+
+// Rebuild cells and Verlet lists of the replicas with flags[r] != 0.
+aqs_status rebuild(aqs_system* s, const std::vector<uint8_t>& flags, int depth = 0) {
+  const int D = s->dim;
+  bool any = false;
+  for (int r = 0; r < s->R; r++) {
+    if (!flags[r]) continue;
+    any = true;
+    double w[3];
+    cell_widths(D, s->geom[r].H, w);
+    int ncell = 1;
+    for (int c = 0; c < D; c++) {
+      int k = (int)std::floor(w[c] / s->rlist);
+      if (k < 3)
+        return fail(AQS_ERR_BOX_TOO_SMALL,
+                    "replica %d: perpendicular cell width %.4g below 3 (rc+skin) = %.4g", r, w[c],
+                    3 * s->rlist);
+      k = std::min(k, 1024);
+      s->geom[r].nc[c] = k;
+      ncell *= k;
+    }
+    if (D == 2) s->geom[r].nc[2] = 1;
+    s->geom[r].ncell = ncell;
+  }
+  if (!any) return AQS_OK;
+  int total = 0;
+  std::vector<int32_t> cell_rep;
+  for (int r = 0; r < s->R; r++) {
+    s->geom[r].cell_off = total;
+    total += s->geom[r].ncell + 1;
+  }
+  cell_rep.resize(total);
+  for (int r = 0; r < s->R; r++)
+    for (int c = 0; c <= s->geom[r].ncell; c++) cell_rep[s->geom[r].cell_off + c] = r;
+  if (total > s->cells_cap) {
+    dfree(s, s->count);
+    dfree(s, s->cstart);
+    dfree(s, s->cell_rep);
+    s->cells_cap = std::max(total, 2 * s->cells_cap);
+    AQS_TRY(alloc_arr(s, &s->count, s->cells_cap));
+    AQS_TRY(alloc_arr(s, &s->cstart, s->cells_cap));
+    AQS_TRY(alloc_arr(s, &s->cell_rep, s->cells_cap));
+  }
+  s->total_cells = total;
+  CUDA_TRY(cudaMemcpyAsync(s->cell_rep, cell_rep.data(), sizeof(int32_t) * total,
+                           cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(s->d_flag, flags.data(), s->R, cudaMemcpyHostToDevice, s->stream));
+  AQS_TRY(upload_geom(s));
+  {
+    BuildArgs a = build_args(s);
+    CUDA_TRY(cudaMemsetAsync(s->count, 0, sizeof(int32_t) * total, s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->overflow, 0, sizeof(int32_t) * s->R, s->stream));
+    CUDA_TRY(launch_rebuild_bin(D, a, s->R, s->stream));
+    CUDA_TRY(launch_rebuild_sort(D, a, total, s->stream));
+    CUDA_TRY(launch_rebuild_verlet(D, a, s->stream));
+    std::vector<int32_t> over(s->R);
+    CUDA_TRY(cudaMemcpyAsync(over.data(), s->overflow, sizeof(int32_t) * s->R,
+                             cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    int need = 0;
+    for (int r = 0; r < s->R; r++) need = std::max(need, over[r]);
+    if (need > 0) {
+      // grow the list; every replica's block moves, so all of them are rebuilt
+      if (depth >= 6) return fail(AQS_ERR_NLIST_OVERFLOW, "neighbour list keeps overflowing");
+      s->cap = std::max((int)(s->cap * 1.5), need + 16);
+      AQS_TRY(layout_lists(s));
+      return rebuild(s, std::vector<uint8_t>(s->R, 1), depth + 1);
+    }
+  }
+  for (int r = 0; r < s->R; r++)
+    if (flags[r]) s->geom[r].tilt_b = s->geom[r].H[0 * D + 1];
+  AQS_TRY(upload_geom(s));
+  return AQS_OK;
+}
+
+aqs_status rebuild_all(aqs_system* s) { return rebuild(s, std::vector<uint8_t>(s->R, 1)); }
+
+void make_coef(aqs_system* s, const aqs_potential& p) {
+  s->rcmax = 0.0;
+  for (int a = 0; a < s->nt; a++)
+    for (int b = 0; b < s->nt; b++) {
+      int k = a * s->nt + b;
+      double sig = p.sigma[a * s->nt + b], eps = p.eps[a * s->nt + b];
+      double rc = p.rc_factor * sig;
+      PairCoef& c = s->coef[k];
+      double s6 = std::pow(sig, 6.0);
+      c.A = -48.0 * eps * s6 * s6;
+      c.B = 24.0 * eps * s6;
+      c.C = -lj_du(rc, sig, eps);
+      c.rc = rc;
+      c.rc2 = rc * rc;
+      c.rl2 = (rc + s->skin) * (rc + s->skin);
+      c.e12 = 4.0 * eps * s6 * s6;
+      c.e6 = 4.0 * eps * s6;
+      c.Uc = lj_u(rc, sig, eps);
+      c.dUc = lj_du(rc, sig, eps);
+      c.Af = (float)c.A;
+      c.Bf = (float)c.B;
+      c.Cf = (float)c.C;
+      c.rc2f = (float)c.rc2;
+      double rl = (rc + s->skin) * (1.0 + 1e-6) + 1e-6;  // FP32 rounding margin
+      s->rl2f[k] = (float)(rl * rl);
+      s->rcmax = std::max(s->rcmax, rc);
+    }
+  s->rlist = s->rcmax + s->skin;
+}
+
+FireDev fire_dev(const aqs_fire_params* f) {
+  FireDev d;
+  d.dt0 = f->dt0;
+  d.alpha0 = f->alpha0;
+  d.f_inc = f->f_inc;
+  d.f_dec = f->f_dec;
+  d.f_alpha = f->f_alpha;
+  d.dt_max = f->dt_max;
+  d.dt_min = f->dt_min;
+  d.max_step = f->max_step;
+  d.tol = f->tol;
+  d.ref_ratio = f->ref_ratio;
+  d.ref_dmax = f->ref_dmax;
+  d.n_min = f->n_min;
+  d.max_iter = f->max_iter;
+  return d;
+}
+
+MinArgs min_args(aqs_system* s, const aqs_fire_params* f) {
+  MinArgs a;
+  a.geom = s->d_geom;
+  a.state = s->d_state;
+  a.work = s->d_work;
+  a.x = s->x;
+  a.v = s->v;
+  a.fref = s->fref;
+  a.dl = s->dl;
+  a.xs = s->xs;
+  a.xb = s->xb;
+  a.type = s->type;
+  a.cell = s->cell;
+  a.nb = s->nb;
+  a.nnb = s->nnb;
+  a.coef = s->d_coef;
+  a.ntot = s->ntot;
+  a.nt = s->nt;
+  a.fire = fire_dev(f);
+  a.skin = s->skin;
+  a.rlist = s->rlist;
+  return a;
+}
+
+// Non-affine displacement max_a |(x_a - xs_a) - mean| of each listed replica.
+aqs_status nonaffine(aqs_system* s, const std::vector<int>& reps, std::vector<double>& out) {
+  std::vector<CmpJob> jobs(reps.size());
+  for (size_t k = 0; k < reps.size(); k++) {
+    int r = reps[k];
+    CmpJob& J = jobs[k];
+    J.a = s->x + s->off[r];
+    J.b = s->xs + s->off[r];
+    J.sa = 1;
+    J.sc = s->ntot;
+    J.sb = 1;
+    J.sc2 = s->ntot;
+    std::memcpy(J.H, s->geom[r].H, sizeof(J.H));
+    J.n = (int)s->n[r];
+  }
+  out.assign(reps.size(), 0.0);
+  if (reps.empty()) return AQS_OK;
+  CUDA_TRY(cudaMemcpyAsync(s->d_jobs, jobs.data(), sizeof(CmpJob) * jobs.size(),
+                           cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(launch_compare(s->dim, s->d_jobs, (int)jobs.size(), s->d_cmp, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(out.data(), s->d_cmp, sizeof(double) * reps.size(),
+                           cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return AQS_OK;
+}
+
+// Minimise the replicas with mask[r]; fills res[r] for those.
+aqs_status minimize_impl(aqs_system* s, const aqs_fire_params* f, const std::vector<uint8_t>& mask,
+                         aqs_min_result* res) {
+  std::vector<int> todo;
+  for (int r = 0; r < s->R; r++)
+    if (mask[r]) {
+      todo.push_back(r);
+      s->st[r].fresh = 1;
+      s->st[r].status = kStatusRunning;
+    }
+  if (todo.empty()) return AQS_OK;
+  AQS_TRY(upload_state(s));
+  std::vector<int64_t> rebuilds(s->R, 0);
+  std::vector<int> order_work;
+  for (int pass = 0; pass < 100000 && !todo.empty(); pass++) {
+    // group the pending replicas by cluster size; one launch per group
+    std::vector<int> Cs;
+    for (int r : todo) Cs.push_back(s->geom[r].C);
+    std::sort(Cs.begin(), Cs.end());
+    Cs.erase(std::unique(Cs.begin(), Cs.end()), Cs.end());
+    order_work.clear();
+    std::vector<std::pair<int, int>> groups;  // (start, count)
+    for (int C : Cs) {
+      int start = (int)order_work.size();
+      for (int r : todo)
+        if (s->geom[r].C == C) order_work.push_back(r);
+      groups.push_back({start, (int)order_work.size() - start});
+    }
+    CUDA_TRY(cudaMemcpyAsync(s->d_work, order_work.data(), sizeof(int) * order_work.size(),
+                             cudaMemcpyHostToDevice, s->stream));
+    MinArgs a = min_args(s, f);
+    for (size_t gi = 0; gi < groups.size(); gi++) {
+      int C = Cs[gi];
+      int npc = 0;
+      for (int k = 0; k < groups[gi].second; k++)
+        npc = std::max(npc, s->geom[order_work[groups[gi].first + k]].npc);
+      a.work = s->d_work + groups[gi].first;
+      CUDA_TRY(launch_minimize(s->dim, s->prec == AQS_MIXED, a, groups[gi].second, C, npc,
+                               s->stream));
+    }
+    AQS_TRY(download_state(s));
+    std::vector<uint8_t> flags(s->R, 0);
+    std::vector<int> next;
+    for (int r : todo)
+      if (s->st[r].status == kStatusRebuild) {
+        flags[r] = 1;
+        next.push_back(r);
+        rebuilds[r]++;
+      }
+    if (!next.empty()) AQS_TRY(rebuild(s, flags));
+    todo.swap(next);
+  }
+  if (!todo.empty()) return fail(AQS_ERR_TIMEOUT, "minimiser kept asking for list rebuilds");
+  std::vector<int> reps;
+  for (int r = 0; r < s->R; r++)
+    if (mask[r]) reps.push_back(r);
+  std::vector<double> na;
+  AQS_TRY(nonaffine(s, reps, na));
+  aqs_status first = AQS_OK;
+  for (size_t k = 0; k < reps.size(); k++) {
+    int r = reps[k];
+    const RepState& t = s->st[r];
+    if (res) {
+      aqs_min_result& o = res[r];
+      o.iters = t.iters;
+      o.evals64 = t.evals64;
+      o.rebuilds = rebuilds[r];
+      o.energy = t.E;
+      o.fmax = t.fmax;
+      o.tau = t.tau;
+      o.nonaffine = na[k];
+      o.status = t.status;
+    }
+    if (t.status != AQS_OK && first == AQS_OK) {
+      first = (aqs_status)t.status;
+      fail(first, "replica %d: minimiser status %d after %lld iterations (fmax %.3g)", r,
+           t.status, (long long)t.iters, t.fmax);
+    }
+  }
+  return first;
+}
+
+aqs_status affine_impl(aqs_system* s, const std::vector<double>& dg) {
+  const int D = s->dim;
+  bool any = false;
+  for (int r = 0; r < s->R; r++) {
+    if (dg[r] == 0.0) continue;
+    any = true;
+    s->geom[r].H[0 * D + 1] += dg[r] * s->geom[r].H[1 * D + 1];
+  }
+  if (!any) return AQS_OK;
+  AQS_TRY(upload_geom(s));
+  CUDA_TRY(cudaMemcpyAsync(s->d_dg, dg.data(), sizeof(double) * s->R, cudaMemcpyHostToDevice,
+                           s->stream));
+  CUDA_TRY(launch_affine(s->x, s->xb, s->d_rep_of, s->d_dg, s->ntot, s->stream));
+  return AQS_OK;
+}
+
+aqs_status alloc_system(aqs_system* s) {
+  const int D = s->dim;
+  const int64_t N = s->ntot;
+  AQS_TRY(alloc_arr(s, &s->d_geom, s->R));
+  AQS_TRY(alloc_arr(s, &s->d_state, s->R));
+  AQS_TRY(alloc_arr(s, &s->d_coef, AQS_MAX_TYPES * AQS_MAX_TYPES));
+  AQS_TRY(alloc_arr(s, &s->d_work, s->R));
+  AQS_TRY(alloc_arr(s, &s->d_flag, s->R));
+  AQS_TRY(alloc_arr(s, &s->d_rep_of, N));
+  AQS_TRY(alloc_arr(s, &s->x, D * N));
+  AQS_TRY(alloc_arr(s, &s->v, D * N));
+  AQS_TRY(alloc_arr(s, &s->xs, D * N));
+  AQS_TRY(alloc_arr(s, &s->xb, D * N));
+  AQS_TRY(alloc_arr(s, &s->fref, D * N));
+  AQS_TRY(alloc_arr(s, &s->dl, D * N));
+  AQS_TRY(alloc_arr(s, &s->tmp, 3 * D * N));
+  AQS_TRY(alloc_arr(s, &s->d_dg, s->R));
+  AQS_TRY(alloc_arr(s, &s->ubuf, D * s->nmax));
+  AQS_TRY(alloc_arr(s, &s->ubuf2, D * s->nmax));
+  AQS_TRY(alloc_arr(s, &s->type, N));
+  AQS_TRY(alloc_arr(s, &s->perm, N));
+  AQS_TRY(alloc_arr(s, &s->inv, N));
+  AQS_TRY(alloc_arr(s, &s->cell, N));
+  AQS_TRY(alloc_arr(s, &s->key, N));
+  AQS_TRY(alloc_arr(s, &s->itmp, 3 * N));
+  AQS_TRY(alloc_arr(s, &s->nnb, N));
+  AQS_TRY(alloc_arr(s, &s->order, N));
+  AQS_TRY(alloc_arr(s, &s->overflow, s->R));
+  AQS_TRY(alloc_arr(s, &s->d_jobs, std::max(s->R, 64)));
+  AQS_TRY(alloc_arr(s, &s->d_cmp, std::max(s->R, 64)));
+  AQS_TRY(alloc_arr(s, &s->d_partial, 2 * (energy_blocks((int)s->nmax) + 1)));
+  AQS_TRY(alloc_arr(s, &s->d_i64, 4 * std::max(s->R, 64)));
+  AQS_TRY(alloc_arr(s, &s->d_shift, std::max(s->R, 64)));
+  CUDA_TRY(cudaMemsetAsync(s->v, 0, sizeof(double) * D * N, s->stream));
+  CUDA_TRY(cudaMemsetAsync(s->dl, 0, sizeof(double) * D * N, s->stream));
+  CUDA_TRY(cudaMemsetAsync(s->fref, 0, sizeof(double) * D * N, s->stream));
+  AQS_TRY(layout_lists(s));
+  return AQS_OK;
+}
+
+// Common part of system creation (positions/types uploaded by the caller).
+aqs_status init_system(aqs_system* s, int dim, int R, const int64_t* n, const aqs_potential& pot,
+                       int prec, double skin, int cap, int C_override, cudaStream_t stream,
+                       void* (*ua)(size_t, void*), void (*uf)(void*, void*), void* actx) {
+  s->dim = dim;
+  s->R = R;
+  s->nt = pot.n_types;
+  s->pot = pot;
+  s->prec = prec;
+  s->skin = skin > 0.0 ? skin : 0.3;
+  s->cap = cap > 0 ? cap : (dim == 2 ? 64 : 160);
+  s->C_override = C_override;
+  s->stream = stream;
+  s->ualloc = ua;
+  s->ufree = uf;
+  s->actx = actx;
+  s->n.assign(n, n + R);
+  s->off.resize(R);
+  s->ntot = 0;
+  s->nmax = 0;
+  for (int r = 0; r < R; r++) {
+    s->off[r] = s->ntot;
+    s->ntot += n[r];
+    s->nmax = std::max(s->nmax, n[r]);
+  }
+  make_coef(s, pot);
+  s->geom.assign(R, RepGeom{});
+  s->st.assign(R, RepState{});
+  s->mean_nb.assign(R, 0.0);
+  for (int r = 0; r < R; r++) {
+    RepGeom& g = s->geom[r];
+    g.off = s->off[r];
+    g.n = (int)n[r];
+    int C = C_override > 0 ? C_override : auto_cluster(R, n[r]);
+    C = std::max(1, std::min(C, kMaxCluster));
+    g.C = C;
+    g.npc = (int)((n[r] + C - 1) / C);
+    s->st[r].fresh = 1;
+    s->st[r].status = AQS_OK;
+  }
+  AQS_TRY(alloc_system(s));
+  CUDA_TRY(cudaMemcpyAsync(s->d_coef, s->coef, sizeof(s->coef), cudaMemcpyHostToDevice, stream));
+  std::vector<int32_t> rep_of(s->ntot), ident(s->ntot);
+  for (int r = 0; r < R; r++)
+    for (int64_t i = 0; i < n[r]; i++) {
+      rep_of[s->off[r] + i] = r;
+      ident[s->off[r] + i] = (int32_t)i;
+    }
+  CUDA_TRY(cudaMemcpyAsync(s->d_rep_of, rep_of.data(), sizeof(int32_t) * s->ntot,
+                           cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(s->perm, ident.data(), sizeof(int32_t) * s->ntot,
+                           cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(s->inv, ident.data(), sizeof(int32_t) * s->ntot,
+                           cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  AQS_TRY(upload_state(s));
+  return AQS_OK;
+}
+
+aqs_status check_box(aqs_system* s, int r, const double* H) {
+  const int D = s->dim;
+  for (int a = 0; a < D; a++)
+    for (int b = 0; b < a; b++)
+      if (H[a * D + b] != 0.0) return fail(AQS_ERR_INVALID_ARG, "cell must be upper triangular");
+  if (D == 3 && (H[0 * 3 + 2] != 0.0 || H[1 * 3 + 2] != 0.0))
+    return fail(AQS_ERR_UNSUPPORTED, "3D cells may only tilt in xy");
+  for (int a = 0; a < D; a++)
+    if (!(H[a * D + a] > 0.0)) return fail(AQS_ERR_INVALID_ARG, "cell diagonal must be positive");
+  double w[3];
+  cell_widths(D, H, w);
+  for (int c = 0; c < D; c++)
+    if (!(s->rlist * 3.0 <= w[c]))
+      return fail(AQS_ERR_BOX_TOO_SMALL, "replica %d: width %.4g < 3 (rc+skin) = %.4g", r, w[c],
+                  3.0 * s->rlist);
+  return AQS_OK;
+}
+
+// Copy user-order positions (host or device) of replica r into the system.
+aqs_status put_positions(aqs_system* s, int r, const double* pos) {
+  const int D = s->dim;
+  size_t bytes = sizeof(double) * D * s->n[r];
+  const double* src = pos;
+  if (!is_device_ptr(pos)) {
+    CUDA_TRY(cudaMemcpyAsync(s->ubuf, pos, bytes, cudaMemcpyHostToDevice, s->stream));
+    src = s->ubuf;
+  }
+  CUDA_TRY(launch_scatter_user(src, s->x, s->ntot, s->off[r], (int)s->n[r], s->perm, D, s->stream));
+  CUDA_TRY(cudaMemsetAsync(s->v, 0, sizeof(double) * D * s->ntot, s->stream));
+  return AQS_OK;
+}
+
+aqs_status fetch_positions(const aqs_system* s, int r, double* out) {
+  const int D = s->dim;
+  bool dev = is_device_ptr(out);
+  double* dst = dev ? out : s->ubuf;
+  CUDA_TRY(launch_gather_user(s->x, s->ntot, s->off[r], (int)s->n[r], s->perm, D, dst, s->stream));
+  if (!dev)
+    CUDA_TRY(cudaMemcpyAsync(out, s->ubuf, sizeof(double) * D * s->n[r], cudaMemcpyDeviceToHost,
+                             s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return AQS_OK;
+}
+
+void destroy(aqs_system* s) {
+  if (!s) return;
+  if (s->chains) destroy(s->chains);
+  cudaStreamSynchronize(s->stream);
+  for (auto& a : s->allocs) {
+    if (s->ufree) s->ufree(a.p, s->actx);
+    else cudaFree(a.p);
+  }
+  s->allocs.clear();
+  delete s;
+}
+
+// ---- two-level parallel stepping (Algorithm 1) ----
+aqs_status ensure_chains(aqs_system* s, int src, int P) {
+  if (s->chains && s->chains->R == P && s->chains->n[0] == s->n[src]) return AQS_OK;
+  if (s->chains) destroy(s->chains);
+  s->chains = nullptr;
+  aqs_system* c = new aqs_system();
+  std::vector<int64_t> n(P, s->n[src]);
+  aqs_status st = init_system(c, s->dim, P, n.data(), s->pot, s->prec, s->skin, s->cap, 0,
+                              s->stream, s->ualloc, s->ufree, s->actx);
+  if (st != AQS_OK) {
+    destroy(c);
+    return st;
+  }
+  const size_t per = (size_t)s->dim * s->n[src];
+  c->snap = static_cast<double*>(dalloc(c, sizeof(double) * per * P));
+  c->ends = static_cast<double*>(dalloc(c, sizeof(double) * per * P));
+  if (!c->snap || !c->ends) {
+    destroy(c);
+    return fail(AQS_ERR_OOM, "chain snapshot allocation failed");
+  }
+  s->chains = c;
+  return AQS_OK;
+}
+
+// Copies replica `sr` of system a into replicas `drs` of system b, the copy k
+// sheared by shift[k]; velocities cleared.  Lists are not copied (rebuilt).
+aqs_status copy_replicas(aqs_system* a, int sr, aqs_system* b, const std::vector<int>& drs,
+                         const std::vector<double>& shift) {
+  RepCopy c;
+  c.sx = a->x;
+  c.sxb = a->xb;
+  c.stype = a->type;
+  c.sperm = a->perm;
+  c.sinv = a->inv;
+  c.scell = a->cell;
+  c.snnb = a->nnb;
+  c.snb = a->nb;
+  c.sN = a->ntot;
+  c.soff = a->off[sr];
+  c.snb_off = a->geom[sr].nb_off;
+  c.dx = b->x;
+  c.dxb = b->xb;
+  c.dv = b->v;
+  c.dtype = b->type;
+  c.dperm = b->perm;
+  c.dinv = b->inv;
+  c.dcell = b->cell;
+  c.dnnb = b->nnb;
+  c.dnb = b->nb;
+  c.dN = b->ntot;
+  std::vector<int64_t> offs(2 * drs.size());
+  for (size_t k = 0; k < drs.size(); k++) {
+    offs[k] = b->off[drs[k]];
+    offs[drs.size() + k] = b->geom[drs[k]].nb_off;
+  }
+  CUDA_TRY(cudaMemcpyAsync(b->d_i64, offs.data(), sizeof(int64_t) * offs.size(),
+                           cudaMemcpyHostToDevice, b->stream));
+  CUDA_TRY(cudaMemcpyAsync(b->d_shift, shift.data(), sizeof(double) * shift.size(),
+                           cudaMemcpyHostToDevice, b->stream));
+  c.doff = b->d_i64;
+  c.dnb_off = b->d_i64 + drs.size();
+  c.shift = b->d_shift;
+  c.n = (int)a->n[sr];
+  c.cap = 0;  // lists are rebuilt for the new owner layout
+  c.ncopy = (int)drs.size();
+  c.D = a->dim;
+  CUDA_TRY(launch_copy_rep(c, b->stream));
+  const int D = a->dim;
+  for (size_t k = 0; k < drs.size(); k++) {
+    RepGeom& g = b->geom[drs[k]];
+    std::memcpy(g.H, a->geom[sr].H, sizeof(g.H));
+    g.H[0 * D + 1] += shift[k] * g.H[1 * D + 1];
+  }
+  std::vector<uint8_t> flags(b->R, 0);
+  for (int r : drs) flags[r] = 1;
+  return rebuild(b, flags);
+}
+
+aqs_status gather_user(aqs_system* s, int r, double* dst) {
+  CUDA_TRY(launch_gather_user(s->x, s->ntot, s->off[r], (int)s->n[r], s->perm, s->dim, dst,
+                              s->stream));
+  return AQS_OK;
+}
+
+}  // namespace
+
+// =====================================================================
+//                                C ABI
+// =====================================================================
+extern "C" {
+
+void aqs_fire_params_default(aqs_fire_params* f) {
+  if (!f) return;
+  f->dt0 = 0.005;
+  f->alpha0 = 0.1;
+  f->f_inc = 1.1;
+  f->f_dec = 0.5;
+  f->f_alpha = 0.99;
+  f->dt_max = 0.05;
+  f->dt_min = 1e-4;
+  f->max_step = 0.1;
+  f->tol = 1e-10;
+  f->n_min = 5;
+  f->max_iter = 1000000;
+  f->ref_ratio = 30.0;
+  f->ref_dmax = 0.05;
+}
+
+aqs_status aqs_create_system(const aqs_system_desc* d, aqs_system** out) {
+  if (!d || !out) return fail(AQS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) return fail(AQS_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (d->n_replicas < 1 || !d->n_atoms || !d->box || !d->pos || !d->types)
+    return fail(AQS_ERR_INVALID_ARG, "missing replica data");
+  if (d->pot.n_types < 1 || d->pot.n_types > AQS_MAX_TYPES || !(d->pot.rc_factor > 0.0))
+    return fail(AQS_ERR_INVALID_ARG, "bad potential");
+  for (int k = 0; k < d->pot.n_types * d->pot.n_types; k++)
+    if (!(d->pot.sigma[k] > 0.0) || !(d->pot.eps[k] >= 0.0))
+      return fail(AQS_ERR_INVALID_ARG, "sigma must be > 0 and eps >= 0");
+  if (d->precision != AQS_FP64 && d->precision != AQS_MIXED)
+    return fail(AQS_ERR_INVALID_ARG, "bad precision");
+  int64_t ntot = 0;
+  for (int r = 0; r < d->n_replicas; r++) {
+    if (d->n_atoms[r] < 2 || d->n_atoms[r] > 16 * 4096)
+      return fail(AQS_ERR_UNSUPPORTED, "replica %d: atom count %lld outside [2, 65536]", r,
+                  (long long)d->n_atoms[r]);
+    ntot += d->n_atoms[r];
+  }
+  if (d->cluster_size > kMaxCluster) return fail(AQS_ERR_INVALID_ARG, "cluster_size > 16");
+  aqs_system* s = new aqs_system();
+  aqs_status st = init_system(s, d->dim, d->n_replicas, d->n_atoms, d->pot, d->precision, d->skin,
+                              d->nlist_capacity, d->cluster_size, (cudaStream_t)d->stream,
+                              d->alloc, d->free, d->alloc_ctx);
+  if (st != AQS_OK) {
+    destroy(s);
+    return st;
+  }
+  for (int r = 0; r < s->R; r++) {
+    const int64_t npc = s->geom[r].npc;
+    if (npc > 4096) {
+      destroy(s);
+      return fail(AQS_ERR_UNSUPPORTED, "replica %d: %lld atoms per CTA exceeds 4096", r,
+                  (long long)npc);
+    }
+    std::memcpy(s->geom[r].H, d->box + (size_t)r * d->dim * d->dim,
+                sizeof(double) * d->dim * d->dim);
+    st = check_box(s, r, s->geom[r].H);
+    if (st != AQS_OK) {
+      destroy(s);
+      return st;
+    }
+    s->geom[r].tilt_b = s->geom[r].H[1];
+  }
+  // types (validated on the host)
+  std::vector<int32_t> ht(ntot);
+  if (is_device_ptr(d->types)) {
+    if (cudaMemcpy(ht.data(), d->types, sizeof(int32_t) * ntot, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      destroy(s);
+      return fail(AQS_ERR_CUDA, "reading types failed");
+    }
+  } else {
+    std::memcpy(ht.data(), d->types, sizeof(int32_t) * ntot);
+  }
+  for (int64_t i = 0; i < ntot; i++)
+    if (ht[i] < 0 || ht[i] >= s->nt) {
+      destroy(s);
+      return fail(AQS_ERR_INVALID_ARG, "type %d of atom %lld out of range", ht[i], (long long)i);
+    }
+  if (cudaMemcpyAsync(s->type, ht.data(), sizeof(int32_t) * ntot, cudaMemcpyHostToDevice,
+                      s->stream) != cudaSuccess) {
+    destroy(s);
+    return fail(AQS_ERR_CUDA, "uploading types failed");
+  }
+  bool dev = is_device_ptr(d->pos);
+  for (int r = 0; r < s->R; r++) {
+    const double* p = d->pos + (size_t)s->off[r] * s->dim;
+    (void)dev;
+    st = put_positions(s, r, p);
+    if (st != AQS_OK) {
+      destroy(s);
+      return st;
+    }
+  }
+  st = rebuild_all(s);
+  if (st != AQS_OK) {
+    destroy(s);
+    return st;
+  }
+  *out = s;
+  return AQS_OK;
+}
+
+void aqs_destroy_system(aqs_system* s) { destroy(s); }
+
+aqs_status aqs_affine_shear(aqs_system* s, const double* dgamma) {
+  if (!s || !dgamma) return fail(AQS_ERR_INVALID_ARG, "null argument");
+  std::vector<double> dg(dgamma, dgamma + s->R);
+  for (int r = 0; r < s->R; r++) {
+    if (!std::isfinite(dg[r])) return fail(AQS_ERR_INVALID_ARG, "non-finite dgamma");
+    double H[9];
+    std::memcpy(H, s->geom[r].H, sizeof(H));
+    H[1] += dg[r] * H[s->dim + 1];
+    double w[3];
+    cell_widths(s->dim, H, w);
+    if (!(s->rlist * 3.0 <= w[0])) return fail(AQS_ERR_BOX_TOO_SMALL, "tilt too large");
+  }
+  return affine_impl(s, dg);
+}
+
+aqs_status aqs_minimize(aqs_system* s, const aqs_fire_params* f, const uint8_t* mask,
+                        aqs_min_result* out) {
+  if (!s || !f) return fail(AQS_ERR_INVALID_ARG, "null argument");
+  if (!(f->tol > 0.0) || !(f->dt0 > 0.0) || f->max_iter < 0 || !(f->max_step > 0.0))
+    return fail(AQS_ERR_INVALID_ARG, "bad FIRE parameters");
+  std::vector<uint8_t> m(s->R, 1);
+  if (mask)
+    for (int r = 0; r < s->R; r++) m[r] = mask[r] != 0;
+  return minimize_impl(s, f, m, out);
+}
+
+aqs_status aqs_run_sequential(aqs_system* s, const aqs_fire_params* f, double dgamma,
+                              int64_t n_steps, double* energy, double* tau, int64_t* fire_iters,
+                              double* nonaffine_out) {
+  if (!s || !f || n_steps < 0) return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  std::vector<double> dg(s->R, dgamma);
+  std::vector<uint8_t> all(s->R, 1);
+  std::vector<aqs_min_result> res(s->R);
+  for (int64_t k = 0; k < n_steps; k++) {
+    AQS_TRY(aqs_affine_shear(s, dg.data()));
+    AQS_TRY(minimize_impl(s, f, all, res.data()));
+    for (int r = 0; r < s->R; r++) {
+      size_t i = (size_t)k * s->R + r;
+      if (energy) energy[i] = res[r].energy;
+      if (tau) tau[i] = res[r].tau;
+      if (fire_iters) fire_iters[i] = res[r].iters;
+      if (nonaffine_out) nonaffine_out[i] = res[r].nonaffine;
+    }
+  }
+  return AQS_OK;
+}
+
+aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
+                             const aqs_parallel_params* p, aqs_parallel_result* out) {
+  if (!s || !f || !p || !out) return fail(AQS_ERR_INVALID_ARG, "null argument");
+  if (src < 0 || src >= s->R) return fail(AQS_ERR_INVALID_ARG, "replica out of range");
+  if (p->K < 1 || p->P < 1 || p->n_steps < 0 || !std::isfinite(p->dgamma))
+    return fail(AQS_ERR_INVALID_ARG, "bad parallel parameters");
+  if (p->warm_start) return fail(AQS_ERR_UNSUPPORTED, "warm start is not available");
+  const double eq_tol = p->eq_tol > 0.0 ? p->eq_tol : 1e-6;
+  const double ev_thr = p->event_threshold > 0.0 ? p->event_threshold : 1e-2;
+  const int K = p->K, P = p->P, D = s->dim;
+  const int n = (int)s->n[src];
+  AQS_TRY(ensure_chains(s, src, P));
+  aqs_system* c = s->chains;
+  out->iterations = out->accepted_steps = out->rejections = 0;
+  out->fire_iters_total = out->evals64_total = 0;
+  out->n_log = 0;
+  std::vector<double> cE((size_t)P * K), cT((size_t)P * K), cD((size_t)P * K);
+  std::vector<int64_t> cI((size_t)P * K);
+  std::vector<aqs_min_result> res(P);
+  int64_t n_cur = 0;
+  const size_t per = (size_t)D * n;
+  while (n_cur < p->n_steps && (p->max_iterations <= 0 || out->iterations < p->max_iterations)) {
+    const int64_t rem = p->n_steps - n_cur;
+    const int P_eff = (int)std::min<int64_t>(P, (rem + K - 1) / K);
+    std::vector<int> Ki(P_eff, K);
+    if (rem < (int64_t)P_eff * K) Ki[P_eff - 1] = (int)(rem - (int64_t)(P_eff - 1) * K);
+    // level I: r^c_iK = F^(i K dgamma) r_star (Eq. 18)
+    std::vector<int> drs(P_eff);
+    std::vector<double> shift(P_eff);
+    for (int i = 0; i < P_eff; i++) {
+      drs[i] = i;
+      shift[i] = (double)i * K * p->dgamma;
+    }
+    AQS_TRY(copy_replicas(s, src, c, drs, shift));
+    // level II (Eq. 19): first F on every chain -> outgoing configurations
+    std::vector<uint8_t> mask(P, 0);
+    for (int i = 0; i < P_eff; i++) mask[i] = 1;
+    AQS_TRY(minimize_impl(c, f, mask, res.data()));
+    for (int i = 0; i < P_eff; i++) {
+      out->fire_iters_total += res[i].iters;
+      out->evals64_total += res[i].evals64;
+    }
+    for (int i = 1; i < P_eff; i++) AQS_TRY(gather_user(c, i, c->snap + per * i));
+    // K fine AQS steps on every chain (the shortened last chain drops out)
+    for (int k = 0; k < K; k++) {
+      std::vector<double> dg(P, 0.0);
+      std::vector<uint8_t> mk(P, 0);
+      bool any = false;
+      for (int i = 0; i < P_eff; i++)
+        if (k < Ki[i]) {
+          dg[i] = p->dgamma;
+          mk[i] = 1;
+          any = true;
+        }
+      if (!any) break;
+      AQS_TRY(affine_impl(c, dg));
+      AQS_TRY(minimize_impl(c, f, mk, res.data()));
+      for (int i = 0; i < P_eff; i++)
+        if (mk[i]) {
+          cE[(size_t)i * K + k] = res[i].energy;
+          cT[(size_t)i * K + k] = res[i].tau;
+          cI[(size_t)i * K + k] = res[i].iters;
+          cD[(size_t)i * K + k] = res[i].nonaffine;
+          out->fire_iters_total += res[i].iters;
+          out->evals64_total += res[i].evals64;
+        }
+    }
+    // sequential equality check (Eq. 20): end of chain i-1 vs F(r^c_iK)
+    std::vector<double> m(P_eff, 0.0);
+    if (P_eff > 1) {
+      std::vector<CmpJob> jobs(P_eff - 1);
+      for (int i = 1; i < P_eff; i++) {
+        AQS_TRY(gather_user(c, i - 1, c->ends + per * (i - 1)));
+        CmpJob& J = jobs[i - 1];
+        J.a = c->ends + per * (i - 1);
+        J.b = c->snap + per * i;
+        J.sa = D;
+        J.sc = 1;
+        J.sb = D;
+        J.sc2 = 1;
+        std::memcpy(J.H, c->geom[i - 1].H, sizeof(J.H));  // both at strain i K dgamma
+        J.n = n;
+      }
+      CUDA_TRY(cudaMemcpyAsync(c->d_jobs, jobs.data(), sizeof(CmpJob) * jobs.size(),
+                               cudaMemcpyHostToDevice, c->stream));
+      CUDA_TRY(launch_compare(D, c->d_jobs, (int)jobs.size(), c->d_cmp, c->stream));
+      CUDA_TRY(cudaMemcpyAsync(m.data() + 1, c->d_cmp, sizeof(double) * (P_eff - 1),
+                               cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    int first_fail = -1;
+    int64_t q = Ki[0];
+    for (int i = 1; i < P_eff; i++) {
+      bool eq = m[i] < eq_tol;
+      if (out->n_log < out->log_cap) {
+        int64_t j = out->n_log;
+        if (out->log_iter) out->log_iter[j] = out->iterations;
+        if (out->log_i) out->log_i[j] = i;
+        if (out->log_eq) out->log_eq[j] = eq ? 1 : 0;
+        if (out->log_m) out->log_m[j] = m[i];
+      }
+      out->n_log++;
+      if (!eq) {
+        first_fail = i;
+        break;
+      }
+      q += Ki[i];
+    }
+    const int last = first_fail < 0 ? P_eff - 1 : first_fail - 1;
+    int64_t kk = n_cur;
+    for (int i = 0; i <= last; i++)
+      for (int j = 0; j < Ki[i]; j++, kk++) {
+        size_t src_i = (size_t)i * K + j;
+        if (out->energy) out->energy[kk] = cE[src_i];
+        if (out->tau) out->tau[kk] = cT[src_i];
+        if (out->fire_iters) out->fire_iters[kk] = cI[src_i];
+        if (out->nonaffine) out->nonaffine[kk] = cD[src_i];
+        if (out->event) out->event[kk] = cD[src_i] > ev_thr ? 1 : 0;
+      }
+    // r_star <- r_q: the end of chain `last`
+    AQS_TRY(copy_replicas(c, last, s, std::vector<int>{src}, std::vector<double>{0.0}));
+    n_cur += q;
+    out->accepted_steps += q;
+    out->iterations++;
+    if (first_fail >= 0) out->rejections++;
+  }
+  return AQS_OK;
+}
+
+aqs_status aqs_compare_configs(const aqs_system* a, int ra, const aqs_system* b, int rb,
+                               double tol, double* max_disp, int* equal) {
+  if (!a || !b) return fail(AQS_ERR_INVALID_ARG, "null system");
+  if (ra < 0 || ra >= a->R || rb < 0 || rb >= b->R) return fail(AQS_ERR_INVALID_ARG, "bad replica");
+  if (a->n[ra] != b->n[rb] || a->dim != b->dim)
+    return fail(AQS_ERR_INVALID_ARG, "replicas differ in size or dimension");
+  aqs_system* sa = const_cast<aqs_system*>(a);
+  aqs_system* sb = const_cast<aqs_system*>(b);
+  CUDA_TRY(cudaStreamSynchronize(sb->stream));
+  AQS_TRY(gather_user(sa, ra, sa->ubuf));
+  AQS_TRY(gather_user(sb, rb, sa->ubuf2));
+  CUDA_TRY(cudaStreamSynchronize(sb->stream));
+  CmpJob J;
+  J.a = sa->ubuf;
+  J.b = sa->ubuf2;
+  J.sa = a->dim;
+  J.sc = 1;
+  J.sb = a->dim;
+  J.sc2 = 1;
+  std::memcpy(J.H, a->geom[ra].H, sizeof(J.H));
+  J.n = (int)a->n[ra];
+  CUDA_TRY(cudaMemcpyAsync(sa->d_jobs, &J, sizeof(J), cudaMemcpyHostToDevice, sa->stream));
+  CUDA_TRY(launch_compare(a->dim, sa->d_jobs, 1, sa->d_cmp, sa->stream));
+  double m = 0.0;
+  CUDA_TRY(cudaMemcpyAsync(&m, sa->d_cmp, sizeof(double), cudaMemcpyDeviceToHost, sa->stream));
+  CUDA_TRY(cudaStreamSynchronize(sa->stream));
+  if (max_disp) *max_disp = m;
+  if (equal) *equal = m < tol ? 1 : 0;
+  return AQS_OK;
+}
+
+int aqs_num_replicas(const aqs_system* s) { return s ? s->R : 0; }
+int64_t aqs_num_atoms(const aqs_system* s, int r) {
+  return (s && r >= 0 && r < s->R) ? s->n[r] : 0;
+}
+
+aqs_status aqs_get_positions(const aqs_system* s, int r, double* out) {
+  if (!s || !out || r < 0 || r >= s->R) return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  return fetch_positions(s, r, out);
+}
+
+aqs_status aqs_set_positions(aqs_system* s, int r, const double* pos) {
+  if (!s || !pos || r < 0 || r >= s->R) return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  AQS_TRY(put_positions(s, r, pos));
+  s->st[r].fresh = 1;
+  AQS_TRY(upload_state(s));
+  std::vector<uint8_t> flags(s->R, 0);
+  flags[r] = 1;
+  return rebuild(s, flags);
+}
+
+aqs_status aqs_get_box(const aqs_system* s, int r, double* H) {
+  if (!s || !H || r < 0 || r >= s->R) return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  std::memcpy(H, s->geom[r].H, sizeof(double) * s->dim * s->dim);
+  return AQS_OK;
+}
+
+aqs_status aqs_set_box(aqs_system* s, int r, const double* H) {
+  if (!s || !H || r < 0 || r >= s->R) return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  AQS_TRY(check_box(s, r, H));
+  std::memcpy(s->geom[r].H, H, sizeof(double) * s->dim * s->dim);
+  std::vector<uint8_t> flags(s->R, 0);
+  flags[r] = 1;
+  return rebuild(s, flags);
+}
+
+aqs_status aqs_energy_forces(aqs_system* s, int r, double* energy, double* forces, double* tau) {
+  if (!s || r < 0 || r >= s->R) return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  std::vector<uint8_t> flags(s->R, 0);
+  flags[r] = 1;
+  AQS_TRY(rebuild(s, flags));
+  const int D = s->dim;
+  const int n = (int)s->n[r];
+  bool dev = forces && is_device_ptr(forces);
+  EnergyArgs a;
+  a.geom = s->d_geom + r;
+  a.x = s->x;
+  a.type = s->type;
+  a.cell = s->cell;
+  a.nb = s->nb;
+  a.nnb = s->nnb;
+  a.coef = s->d_coef;
+  a.forces = forces ? (dev ? forces : s->ubuf) : nullptr;
+  a.partial = s->d_partial;
+  a.ntot = s->ntot;
+  a.nt = s->nt;
+  a.perm = s->perm;  // indexed by the global atom index
+  CUDA_TRY(launch_energy(D, a, n, s->stream));
+  int nb = energy_blocks(n);
+  std::vector<double> part(2 * nb);
+  CUDA_TRY(cudaMemcpyAsync(part.data(), s->d_partial, sizeof(double) * 2 * nb,
+                           cudaMemcpyDeviceToHost, s->stream));
+  if (forces && !dev)
+    CUDA_TRY(cudaMemcpyAsync(forces, s->ubuf, sizeof(double) * D * n, cudaMemcpyDeviceToHost,
+                             s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  double e = 0.0, w = 0.0;
+  for (int k = 0; k < nb; k++) {
+    e += part[2 * k];
+    w += part[2 * k + 1];
+  }
+  const double* H = s->geom[r].H;
+  double vol = D == 2 ? H[0] * H[3] : H[0] * H[4] * H[8];
+  if (energy) *energy = 0.5 * e;
+  if (tau) *tau = 0.5 * w / vol;
+  return AQS_OK;
+}
+
+const char* aqs_last_error(void) { return g_err.c_str(); }
+int64_t aqs_launch_count(void) { return g_launches.load(); }
+
+double aqs_mean_neighbours(const aqs_system* s, int r) {
+  if (!s || r < 0 || r >= s->R) return 0.0;
+  std::vector<int32_t> h(s->n[r]);
+  if (cudaMemcpy(h.data(), s->nnb + s->off[r], sizeof(int32_t) * s->n[r], cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return 0.0;
+  double t = 0.0;
+  for (int32_t v : h) t += v;
+  return t / (double)s->n[r];
+}
+
+int aqs_cluster_size(const aqs_system* s, int r) {
+  return (s && r >= 0 && r < s->R) ? s->geom[r].C : 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (from the workload's accuracy targets):
+  energy per atom: 1e-9 relative (AQS_FP64), 1e-6 relative (AQS_MIXED);
+  positions: 1e-6 sigma by minimum image (after removing the mean shift);
+  plastic-event step indices and Algorithm-1 decisions: identical.
+Single force evaluations are FP64 on both sides and are held to ~1e-11.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import load_golden
+
+pytestmark = pytest.mark.gpu
+
+EV_THR = 1e-2  # plastic event: non-affine jump above 0.01 sigma_AA
+
+
+def mi_disp(a, b, H):
+    """max_i |mi(a_i - b_i) - mean| in numpy (test-side comparison)."""
+    d = np.asarray(a, float) - np.asarray(b, float)
+    dim = H.shape[0]
+    for c in reversed(range(dim)):
+        n = np.round(d[:, c] / H[c, c])
+        d -= n[:, None] * H[:, c][None, :]
+    d -= d.mean(axis=0)
+    return float(np.sqrt((d * d).sum(axis=1)).max())
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_2507_20802_gb300 import aqs
+    aqs.lib()
+    return aqs
+
+
+def make_system(A, syn, x, t, H, prec, **kw):
+    x = np.asarray(x, float)
+    return A.System(x, t, H[None], [len(x)], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
+                    precision=prec, **kw)
+
+
+def oracle_pot(orc, syn, dim):
+    return orc.make_potential(dim, syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR)
+
+
+def jiggled_cubic(syn, m=12, density=1.2, amp=0.05, seed=0):
+    a = (1.0 / density) ** (1.0 / 3.0)
+    g = np.arange(m) * a
+    x = np.array(np.meshgrid(g, g, g, indexing="ij")).reshape(3, -1).T
+    u = syn.uniform(800 + seed, x.size).reshape(x.shape) - 0.5
+    t = (syn.uniform(850 + seed, len(x)) < 0.2).astype(np.int32)
+    return x + amp * u, t, np.eye(3) * (m * a)
+
+
+@pytest.fixture(scope="module")
+def glass256():
+    return load_golden("glass_2d_n256_s0.npz")
+
+
+# ------------------------------------------------------------ force parity
+@pytest.mark.parametrize("case", ["glass", "sheared_glass", "random_start", "cubic3d"])
+def test_energy_forces_match_oracle(A, orc, syn, glass256, case):
+    if case == "cubic3d":
+        x, t, H = jiggled_cubic(syn)
+    elif case == "random_start":
+        x, t, H = syn.random_glass_start(700, 2, seed=5)  # ragged N, huge forces
+    else:
+        x, t, H = glass256["x"], glass256["types"], glass256["H"]
+        if case == "sheared_glass":
+            x, H = orc.affine_shear(x, H, 0.05)
+            x = x + 0.02 * (syn.uniform(31, x.size).reshape(x.shape) - 0.5)
+    s = make_system(A, syn, x, t, H, A.AQS_FP64)
+    E, F, tau = s.energy_forces()
+    Eo, Fo, tauo = orc.energy_forces(oracle_pot(orc, syn, H.shape[0]), x, t, H)
+    scale = max(1.0, np.abs(Fo).max())
+    assert E == pytest.approx(Eo, rel=1e-11, abs=1e-9)
+    assert np.abs(F - Fo).max() <= 1e-11 * scale
+    assert tau == pytest.approx(tauo, rel=1e-10, abs=1e-10)
+    # Newton's third law on the GPU side as well
+    assert np.linalg.norm(F.sum(axis=0)) <= 1e-11 * scale * math.sqrt(len(x))
+
+
+def test_positions_roundtrip_and_device_pointers(A, syn, glass256):
+    torch = pytest.importorskip("torch")
+    x, t, H = glass256["x"], glass256["types"], glass256["H"]
+    xd = torch.tensor(x, device="cuda", dtype=torch.float64)
+    td = torch.tensor(t, device="cuda", dtype=torch.int32)
+    s = A.System(xd, td, H[None], [len(x)], syn.LJ_SIGMA, syn.LJ_EPS, precision=A.AQS_FP64)
+    out = torch.zeros_like(xd)
+    A.aqs_get_positions(s.h, 0, out)
+    assert mi_disp(out.cpu().numpy(), x, H) == 0.0
+    assert np.array_equal(s.box(), H)
+
+
+# ------------------------------------------------------------ one minimisation
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_minimize_after_shear_matches_oracle(A, orc, syn, glass256, prec):
+    x, t, H = glass256["x"], glass256["types"], glass256["H"]
+    P = A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED
+    s = make_system(A, syn, x, t, H, P)
+    s.shear(1e-3)
+    r = s.minimize()[0]
+    xo, Ho = orc.affine_shear(x, H, 1e-3)
+    ro = orc.fire(oracle_pot(orc, syn, 2), orc.make_fire(**syn.FIRE), xo, t, Ho)
+    assert r["status"] == 0 and r["fmax"] < 1e-10
+    rel = 1e-9 if prec == "fp64" else 1e-6
+    assert r["E"] / len(x) == pytest.approx(ro["E"] / len(x), rel=rel)
+    assert np.allclose(s.box(), Ho, rtol=0, atol=1e-14)
+    assert mi_disp(s.positions(), ro["x"], Ho) < 1e-6
+    # the result is a true FP64 minimum also by the library's own FP64 evaluation
+    E2, F2, _ = s.energy_forces()
+    assert np.sqrt((F2 * F2).sum(1)).max() < 1e-10
+    if prec == "mixed":
+        assert r["evals64"] < r["iters"]  # most iterations ran on FP32 pair forces
+
+
+# ------------------------------------------------------------ AQS trajectory
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sequential_aqs_trajectory_matches_golden(A, syn, glass256, prec):
+    """200 steps of dgamma = 1e-4 on the N = 256 glass (stored oracle run)."""
+    gold = load_golden("aqs_2d_n256_s0.npz")
+    x, t, H = glass256["x"], glass256["types"], glass256["H"]
+    P = A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED
+    s = make_system(A, syn, x, t, H, P)
+    n = int(gold["n_steps"])
+    out = s.run_sequential(float(gold["dgamma"]), n)
+    rel = 1e-9 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(out["E"][:, 0], gold["E"], rtol=rel)
+    np.testing.assert_allclose(out["tau"][:, 0], gold["tau"], rtol=1e-6, atol=1e-7)
+    assert np.array_equal(out["D"][:, 0] > EV_THR, gold["D"] > EV_THR)
+    assert mi_disp(s.positions(), gold["x"], gold["H"]) < 1e-6
+    np.testing.assert_allclose(s.box(), gold["H"], rtol=1e-12)
+
+
+# ------------------------------------------------------------ Algorithm 1
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_parallel_stepping_matches_golden(A, syn, glass256, prec):
+    """Algorithm 1 at the paper's increment 1/200, K = 3, P = 4, 30 steps."""
+    gold = load_golden("par_2d_n256_s0.npz")
+    x, t, H = glass256["x"], glass256["types"], glass256["H"]
+    P = A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED
+    s = make_system(A, syn, x, t, H, P)
+    r = s.parallel_step(float(gold["dgamma"]), int(gold["K"]), int(gold["P"]),
+                        int(gold["n_steps"]), eq_tol=float(gold["eq_tol"]))
+    # identical accept/reject decisions
+    assert np.array_equal(r["log_i"], gold["log_i"])
+    assert np.array_equal(r["log_eq"], gold["log_eq"])
+    assert np.array_equal(r["log_iter"], gold["log_iter"])
+    assert r["iterations"] == int(gold["iterations"])
+    rel = 1e-9 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(r["E"], gold["E"], rtol=rel)
+    assert np.array_equal(r["D"] > EV_THR, gold["D"] > EV_THR)
+    assert mi_disp(s.positions(), gold["x"], gold["H"]) < 1e-6
+
+
+def test_parallel_best_case_on_lattice(A, syn):
+    x, t, H = syn.triangular_lattice(24, 24)
+    s = make_system(A, syn, x, t, H, A.AQS_MIXED)
+    K, P, n = 3, 4, 30
+    r = s.parallel_step(1e-3, K, P, n)
+    assert r["iterations"] == math.ceil(n / (P * K))
+    assert r["rejections"] == 0 and np.all(r["log_eq"] == 1)
+    assert r["accepted"] == n
+    assert np.all(r["iters"] == 0)
+
+
+def test_parallel_equals_sequential_on_gpu(A, syn):
+    """Sec. 3.6 / Sec. 4: the accepted trajectory is the sequential one (a
+    property that holds at any size; N = 1024 glass quenched by the oracle)."""
+    g = load_golden("glass_2d_n1024_s0.npz")
+    x, t, H = g["x"], g["types"], g["H"]
+    seq = make_system(A, syn, x, t, H, A.AQS_MIXED)
+    ref = seq.run_sequential(2e-3, 24)
+    par = make_system(A, syn, x, t, H, A.AQS_MIXED)
+    r = par.parallel_step(2e-3, 3, 4, 24)
+    np.testing.assert_allclose(r["E"], ref["E"][:, 0], rtol=1e-9)
+    assert np.array_equal(r["D"] > EV_THR, ref["D"][:, 0] > EV_THR)
+    assert mi_disp(par.positions(), seq.positions(), seq.box()) < 1e-6
+    assert r["iterations"] <= math.ceil(24 / 3)
+
+
+def test_runs_are_deterministic(A, syn, glass256):
+    x, t, H = glass256["x"], glass256["types"], glass256["H"]
+    outs = []
+    for _ in range(2):
+        s = make_system(A, syn, x, t, H, A.AQS_MIXED)
+        r = s.parallel_step(2e-3, 2, 3, 12)
+        outs.append((s.positions(), r["E"], r["iters"], r["log_m"]))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_batched_replicas_match_single_runs(A, syn, glass256):
+    """Replicas batched in one launch give the same minima as separate runs."""
+    x, t, H = glass256["x"], glass256["types"], glass256["H"]
+    R = 5
+    dg = np.array([0.0, 1e-4, 3e-4, 1e-3, 2e-3])
+    s = A.System(np.tile(x, (R, 1)), np.tile(t, R), np.tile(H[None], (R, 1, 1)), [len(x)] * R,
+                 syn.LJ_SIGMA, syn.LJ_EPS, precision=A.AQS_MIXED)
+    s.shear(dg)
+    res = s.minimize()
+    for r in range(R):
+        one = make_system(A, syn, x, t, H, A.AQS_MIXED)
+        one.shear(dg[r])
+        o = one.minimize()[0]
+        assert res[r]["E"] == pytest.approx(o["E"], rel=1e-12)
+        assert mi_disp(s.positions(r), one.positions(), one.box()) < 1e-9
+
+
+def test_full_size_workload_properties(A, syn):
+    """N = 4096 glass, 16 replicas (the benchmark's launch shape): the first
+    forces agree with the oracle on the seeded start; after a batched mixed
+    minimisation every replica is an FP64 minimum."""
+    x, t, H = syn.random_glass_start(4096, 2, seed=0)
+    s = make_system(A, syn, x, t, H, A.AQS_FP64)
+    E, F, tau = s.energy_forces()
+    sample = np.arange(0, 4096, 97)
+    # the oracle's all-pairs forces at the seeded start, compared on a sample
+    import oracle
+    Eo, Fo, _ = oracle.energy_forces(oracle_pot(oracle, syn, 2), x, t, H)
+    assert E == pytest.approx(Eo, rel=1e-11)
+    np.testing.assert_allclose(F[sample], Fo[sample], rtol=1e-10, atol=1e-6)
+    fire = A.fire_params(max_iter=200000)
+    s.minimize(fire)
+    q = s.positions()
+    R = 16
+    b = A.System(np.tile(q, (R, 1)), np.tile(t, R), np.tile(s.box()[None], (R, 1, 1)),
+                 [4096] * R, syn.LJ_SIGMA, syn.LJ_EPS, precision=A.AQS_MIXED)
+    b.shear(np.arange(R) * 1e-3)
+    res = b.minimize()
+    for r in range(R):
+        assert res[r]["status"] == 0
+        _, Fr, _ = b.energy_forces(r)
+        assert np.sqrt((Fr * Fr).sum(1)).max() < 1e-10
