@@ -67,10 +67,13 @@ __global__ void k_copy_nb(RepCopy a) {
 }
 
 cudaError_t launch_copy_rep(const RepCopy& a, cudaStream_t s) {
+  if (a.ncopy <= 0 || a.n <= 0) return cudaSuccess;
   count_launch();
   k_copy_rep<<<nblk((int64_t)a.ncopy * a.n, 256), 256, 0, s>>>(a);
-  count_launch();
-  k_copy_nb<<<nblk((int64_t)a.ncopy * a.cap * a.n, 256), 256, 0, s>>>(a);
+  if (a.cap > 0) {
+    count_launch();
+    k_copy_nb<<<nblk((int64_t)a.ncopy * a.cap * a.n, 256), 256, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
