@@ -1,0 +1,330 @@
+"""Benchmark: converged AQS strain steps per second of two-level parallel
+stepping (Algorithm 1) on one GB300, with FIRE minimisation in mixed precision.
+
+Workload (one "step" = one pass of Algorithm 1's while loop: level I, P batched
+level-II chains of K fine AQS steps each, the equality tests and r_star <- r_q):
+  2D binary Lennard-Jones glass, 65:35 A:B, N = 4096, number density 1.2,
+  shifted-force cutoff 2.5 sigma_ab, uniform random start (seed = rank)
+  quenched on the GPU to |F|max < 1e-10 (untimed set-up), simple shear
+  dgamma = 1e-4, K = 10, P = 16, every step converged to |F|max < 1e-10 (FP64).
+  Inputs are synthetic (seeded) and stand in for the paper's melt-quenched
+  samples.
+
+Reported (one JSON line on rank 0):
+  value    accepted fine strain steps / s, device-timed (CUDA events on the
+           library's stream) over the K timed passes, L2 flushed between passes
+  e2e      the same metric through the public C ABI with host buffers:
+           host -> device positions, the pass, device -> host positions and
+           per-step observables, all inside the timed region
+  roofline the persistent minimiser kernel (FP32 pipe; its FP64 work noted)
+  cpu_baseline  the FP64 oracle on a bounded sample of this workload
+  clocks   SM clocks and throttle reasons sampled during the timed region
+
+``--impl reference`` times the oracle instead (the CPU program this project is
+checked against) on the same workload and prints the same kind of line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ATOMS, P_CHAINS, K_FINE, DGAMMA, GAMMA_END = 4096, 16, 10, 1e-4, 0.2
+METRIC = "converged AQS strain steps/s (two-level parallel stepping, |F|max<1e-10)"
+UNIT = "steps/s"
+# FP32 peak of GB300 from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop
+# (FMA) x 2.07 GHz maximum SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# algorithmic FP32 flops of one relative pair-force visit (both atoms inside
+# the cutoff; FMA counted as 2, reciprocal square root as 1) and FP64 flops of
+# one FP64 pair visit -- counted from minimize.cu
+FLOP32_PER_PAIR = 62
+FLOP64_PER_PAIR = 32
+# mean FIRE iterations per accepted fine step of this workload, used only to
+# express the reference arm's oracle sample in steps/s (measured by this
+# benchmark's own arm; see profiles/bench_cfg1_n4096.md)
+ITERS_PER_STEP_REF = 20000
+
+CONFIG = {"workload": "2D binary LJ glass (65:35, rho=1.2), N=4096, Algorithm 1 with P=16 "
+                      "chains of K=10 fine steps, dgamma=1e-4, FIRE to |F|max<1e-10, mixed "
+                      "precision", "n_atoms": N_ATOMS, "P": P_CHAINS, "K": K_FINE,
+          "dgamma": DGAMMA, "gamma_end": GAMMA_END, "precision": "mixed",
+          "l2": "flushed (256 MiB write) between timed passes"}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                                 else ".", f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200",
+                                          "-i", str(self.gpu)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [v.strip() for v in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_iteration_rate(n_iters: int, seed: int = 0):
+    """FIRE iterations per second of the FP64 oracle on this workload's size
+    (all-pairs forces dominate, so the rate does not depend on the
+    configuration; the seeded start of the workload is used)."""
+    import oracle
+    from paper_2507_20802_gb300 import synthetic as syn
+    oracle.build()
+    x, t, H = syn.random_glass_start(N_ATOMS, 2, seed)
+    pot = oracle.make_potential(2, syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR)
+    fp = oracle.make_fire(**dict(syn.FIRE, max_iter=n_iters, tol=1e-300))
+    t0 = time.perf_counter()
+    r = oracle.fire(pot, fp, x, t, H)
+    dt = time.perf_counter() - t0
+    evals = r["iters"] + 1
+    return evals / dt, evals, dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    per_step = []
+    n_it = 12
+    for i in range(args.warmup + args.steps):
+        rate, evals, dt = oracle_iteration_rate(n_it)
+        if i >= args.warmup:
+            per_step.append((evals, dt))
+    evals = sum(e for e, _ in per_step)
+    secs = sum(d for _, d in per_step)
+    value = (evals / secs) / ITERS_PER_STEP_REF
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(1, len(per_step)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": CONFIG,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n_it} FIRE iterations of the FP64 all-pairs oracle "
+                                       f"at N={N_ATOMS} per step, converted with "
+                                       f"{ITERS_PER_STEP_REF} FIRE iterations per accepted "
+                                       f"fine step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-iters", type=int, default=40)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2507_20802_gb300 import aqs as A, synthetic as syn
+
+    # ---------------- set-up (untimed): seeded start, quench on the GPU
+    x, t, H = syn.random_glass_start(N_ATOMS, 2, seed=rank)
+    s = A.System(x, t, H[None], [N_ATOMS], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
+                 precision=A.AQS_MIXED)
+    fire = A.fire_params()
+    q = s.minimize(A.fire_params(max_iter=2_000_000))[0]
+    assert q["status"] == 0, q
+    n_total = int(round(GAMMA_END / DGAMMA))
+    done = 0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_pass():
+        nonlocal done
+        remaining = n_total - done if n_total > done else P_CHAINS * K_FINE
+        r = s.parallel_step(DGAMMA, K_FINE, P_CHAINS, remaining, fire=fire, max_iterations=1)
+        done += r["accepted"]
+        return r
+
+    for _ in range(args.warmup):
+        one_pass()
+
+    # ---------------- timed passes (device time)
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    A.aqs_reset_kernel_stats()
+    A.aqs_set_kernel_timing(True)
+    launches0 = A.aqs_launch_count()
+    gpu_index = int((os.environ.get("CUDA_VISIBLE_DEVICES") or str(local)).split(",")[0]) \
+        if (os.environ.get("CUDA_VISIBLE_DEVICES") or "").split(",")[0].isdigit() else local
+    accepted, dev_ms, wall, iters, rej = 0, 0.0, 0.0, [], 0
+    barrier()
+    with Clocks(gpu_index) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            w0 = time.perf_counter()
+            e0.record()
+            r = one_pass()
+            e1.record()
+            e1.synchronize()
+            wall += time.perf_counter() - w0
+            dev_ms += e0.elapsed_time(e1)
+            accepted += r["accepted"]
+            rej += r["rejections"]
+            iters.extend(r["iters"].tolist())
+    barrier()
+    gpu_launches = A.aqs_launch_count() - launches0
+    A.aqs_set_kernel_timing(False)
+    st = A.aqs_get_kernel_stats()
+    clocks = clk.summary()
+
+    secs = dev_ms / 1e3
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([secs, float(accepted)], device="cuda", dtype=torch.float64)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        total_steps, secs = float(tt[1]), float(mx[0])
+    else:
+        total_steps = float(accepted)
+    value = total_steps / secs
+
+    # ---------------- end to end through the C ABI with host buffers
+    n_e2e = max(1, args.e2e_steps)
+    pin = torch.empty((N_ATOMS, 2), dtype=torch.float64).pin_memory()
+    A.aqs_get_positions(s.h, 0, pin.numpy())
+    e2e_steps, e2e_wall = 0, 0.0
+    h2d = d2h = 0
+    for _ in range(n_e2e):
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        A.aqs_set_positions(s.h, 0, pin.numpy())           # host -> device
+        r = one_pass()                                      # the pass (host result arrays)
+        A.aqs_get_positions(s.h, 0, pin.numpy())           # device -> host
+        torch.cuda.synchronize()
+        e2e_wall += time.perf_counter() - w0
+        e2e_steps += r["accepted"]
+        h2d = pin.numel() * 8
+        d2h = pin.numel() * 8 + r["accepted"] * (8 + 8 + 8 + 8 + 1)
+    e2e_value = e2e_steps * ws / e2e_wall
+
+    # ---------------- roofline of the persistent minimiser kernel
+    kern_s = st["kernel_ms"] / 1e3
+    flop32 = st["pairs32"] * FLOP32_PER_PAIR
+    flop64 = st["pairs64"] * FLOP64_PER_PAIR
+    achieved = flop32 / kern_s / 1e12 if kern_s > 0 else 0.0
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": None, "kernel": "k_minimize<2,mixed>",
+                "kernel_share_of_step": kern_s / secs if secs > 0 else None,
+                "fp64_tflops": flop64 / kern_s / 1e12 if kern_s > 0 else 0.0,
+                "launches": st["launches"], "avg_launch_ms": st["kernel_ms"] / max(1, st["launches"]),
+                "pair_visits_fp32": st["pairs32"], "pair_visits_fp64": st["pairs64"],
+                "peak_note": "FP32 peak derived from 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+
+    # ---------------- CPU baseline (oracle, rank 0, N = 1 only)
+    cpu = None
+    mean_iters = float(np.mean(iters)) if iters else float("nan")
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, evals, dt = oracle_iteration_rate(args.cpu_iters)
+        cpu = {"value": rate / mean_iters, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{evals} FIRE iterations of the FP64 all-pairs oracle at N={N_ATOMS} "
+                         f"({dt:.1f} s), divided by the {mean_iters:.0f} FIRE iterations per "
+                         f"accepted fine step measured in this run"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": dev_ms / max(1, args.steps), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic", "config": CONFIG,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(gpu_launches), "clocks": clocks, "roofline": roofline,
+                "cpu_baseline": cpu,
+                "detail": {"accepted_steps": int(total_steps), "rejections": rej,
+                           "wall_s": wall, "fire_iters_per_step": mean_iters,
+                           "fp32_evals": st["evals32"], "fp64_evals": st["evals64"],
+                           "glass_quench_iters": q["iters"]}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -224,6 +224,22 @@ aqs_status aqs_energy_forces(aqs_system* sys, int replica, double* energy, doubl
                              double* tau);
 
 /* ---- diagnostics ---- */
+/* Counters of the persistent minimiser kernel, accumulated over all systems
+ * while timing is on (aqs_set_kernel_timing(1)); pair visits count one atom
+ * looking at one list entry (a pair is visited from both sides). */
+typedef struct {
+  int64_t launches;      /* minimiser launches */
+  double kernel_ms;      /* sum of their durations (CUDA events on the system stream) */
+  int64_t evals32;       /* FP32 relative force evaluations (all replicas) */
+  int64_t evals64;       /* FP64 force evaluations (all replicas) */
+  int64_t pairs32;       /* pair visits in FP32 evaluations */
+  int64_t pairs64;       /* pair visits in FP64 evaluations */
+  int64_t atom_iters;    /* atoms x FIRE iterations */
+} aqs_kernel_stats;
+void aqs_set_kernel_timing(int on);
+void aqs_get_kernel_stats(aqs_kernel_stats* out);
+void aqs_reset_kernel_stats(void);
+
 const char* aqs_last_error(void);
 /* number of kernels this library launched in this process */
 int64_t aqs_launch_count(void);

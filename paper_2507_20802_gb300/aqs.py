@@ -75,6 +75,12 @@ class aqs_parallel_result(C.Structure):
                 ("log_eq", C.POINTER(C.c_uint8)), ("log_m", C.POINTER(C.c_double))]
 
 
+class aqs_kernel_stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("kernel_ms", C.c_double), ("evals32", C.c_int64),
+                ("evals64", C.c_int64), ("pairs32", C.c_int64), ("pairs64", C.c_int64),
+                ("atom_iters", C.c_int64)]
+
+
 # exported symbols and their signatures (kept in the order of include/aqs.h)
 _SIGS = {
     "aqs_fire_params_default": (None, [C.POINTER(aqs_fire_params)]),
@@ -99,6 +105,9 @@ _SIGS = {
     "aqs_set_box": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "aqs_energy_forces": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p,
                                     C.POINTER(C.c_double)]),
+    "aqs_set_kernel_timing": (None, [C.c_int]),
+    "aqs_get_kernel_stats": (None, [C.POINTER(aqs_kernel_stats)]),
+    "aqs_reset_kernel_stats": (None, []),
     "aqs_last_error": (C.c_char_p, []),
     "aqs_launch_count": (C.c_int64, []),
     "aqs_mean_neighbours": (C.c_double, [C.c_void_p, C.c_int]),
@@ -274,6 +283,20 @@ def aqs_energy_forces(h, replica, forces=None):
 
 def aqs_launch_count() -> int:
     return int(lib().aqs_launch_count())
+
+
+def aqs_set_kernel_timing(on: bool):
+    lib().aqs_set_kernel_timing(1 if on else 0)
+
+
+def aqs_get_kernel_stats() -> dict:
+    s = aqs_kernel_stats()
+    lib().aqs_get_kernel_stats(C.byref(s))
+    return {k: getattr(s, k) for k, _ in aqs_kernel_stats._fields_}
+
+
+def aqs_reset_kernel_stats():
+    lib().aqs_reset_kernel_stats()
 
 
 # ------------------------------------------------------------ convenience

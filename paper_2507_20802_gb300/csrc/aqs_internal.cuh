@@ -51,6 +51,7 @@ struct RepState {
   double E, fmax, tau;
   int64_t iters;    // FIRE position updates since the minimisation started
   int64_t evals64;  // FP64 force evaluations since the minimisation started
+  int64_t evals32;  // FP32 (relative) force evaluations since the minimisation started
   int npos;
   int status;       // aqs_status; kStatusRebuild while waiting for a rebuild
   int fresh;        // 1: next minimise call starts FIRE from scratch

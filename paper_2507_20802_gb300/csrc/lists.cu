@@ -216,7 +216,31 @@ __global__ void k_verlet(BuildArgs a) {
   if (cnt > a.cap) atomicMax(&a.overflow[r], cnt);
 }
 
+// total list length of each rebuilt replica (one CTA per replica)
+__global__ void k_sum_nnb(BuildArgs a, int64_t* out) {
+  int r = blockIdx.x;
+  if (!a.flag[r]) return;
+  const RepGeom& g = a.geom[r];
+  int64_t t = 0;
+  for (int i = threadIdx.x; i < g.n; i += blockDim.x) t += a.nnb[g.off + i];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  __shared__ int64_t ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += ws[w];
+    out[r] = s;
+  }
+}
+
 static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+cudaError_t launch_sum_nnb(const BuildArgs& a, int n_rep, int64_t* out, cudaStream_t s) {
+  count_launch();
+  k_sum_nnb<<<n_rep, 256, 0, s>>>(a, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_rebuild_bin(int dim, const BuildArgs& a, int n_rep, cudaStream_t s) {
   const int T = 256;

@@ -35,5 +35,6 @@ struct BuildArgs {
 cudaError_t launch_rebuild_bin(int dim, const BuildArgs& a, int n_rep, cudaStream_t s);
 cudaError_t launch_rebuild_sort(int dim, const BuildArgs& a, int total_cells, cudaStream_t s);
 cudaError_t launch_rebuild_verlet(int dim, const BuildArgs& a, cudaStream_t s);
+cudaError_t launch_sum_nnb(const BuildArgs& a, int n_rep, int64_t* out, cudaStream_t s);
 
 }  // namespace aqs

@@ -178,8 +178,15 @@ __device__ __forceinline__ void load_pub64(const Pub<D>* p, double* q) {
 
 constexpr int kModeEval64 = 0, kModeDev = 1;
 
-template <int D, bool MIXED, int APT>
-__global__ void __launch_bounds__(1024, 1) k_minimize(MinArgs A) {
+// Control block written once per iteration by thread 0 of every CTA (all CTAs
+// compute it from bitwise identical totals) and read by the CTA's threads.
+struct Ctl {
+  double dt, ratio, keep;
+  int move, mode, stop, reset;
+};
+
+template <int D, bool MIXED, int APT, bool LSM>
+__global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -193,19 +200,21 @@ __global__ void __launch_bounds__(1024, 1) k_minimize(MinArgs A) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
   const int64_t N = A.ntot;
+  const int lstride = A.npc_launch;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Pub<D>* pub = reinterpret_cast<Pub<D>*>(smem_raw);
-  double* red = reinterpret_cast<double*>(smem_raw + sizeof(Pub<D>) * npc);  // [kNumRed]
-  double* wred = red + kNumRed;                                               // [32][kNumRed]
-  double* tot = wred + 32 * kNumRed;                                          // [kNumRed]
-  double* off64 = tot + kNumRed;                                              // [27][3]
-  float* off32 = reinterpret_cast<float*>(off64 + 27 * 3);                    // [27][3]
-  PairCoef* coef = reinterpret_cast<PairCoef*>(off32 + 27 * 3 + 3);           // [nt*nt]
+  double* red = reinterpret_cast<double*>(smem_raw + sizeof(Pub<D>) * lstride);  // [kNumRed]
+  double* wred = red + kNumRed;                                                   // [32][kNumRed]
+  double* off64 = wred + 32 * kNumRed;                                            // [27][3]
+  float* off32 = reinterpret_cast<float*>(off64 + 27 * 3);                        // [27][3]
+  PairCoef* coef = reinterpret_cast<PairCoef*>(off32 + 27 * 3 + 3);               // [nt*nt]
+  uint32_t* lst = reinterpret_cast<uint32_t*>(coef + A.nt * A.nt);                // [cap][lstride]
   __shared__ Pub<D>* rpub[kMaxCluster];
   __shared__ double* rred[kMaxCluster];
+  __shared__ Ctl ctl;
 
-  // ---- set-up: tables, remote bases, FIRE state ----
+  // ---- set-up: tables, remote bases, list rows, FIRE state ----
   double H[9];
 #pragma unroll
   for (int k = 0; k < 9; k++) H[k] = g.H[k];
@@ -225,35 +234,46 @@ __global__ void __launch_bounds__(1024, 1) k_minimize(MinArgs A) {
   }
   const FireDev fp = A.fire;
   const bool fresh = st->fresh != 0;
+  // FIRE scalars: meaningful in thread 0 only
   double dt = fresh ? fp.dt0 : st->dt;
   double alpha = fresh ? fp.alpha0 : st->alpha;
   int npos = fresh ? 0 : st->npos;
   int64_t iters = fresh ? 0 : st->iters;
   int64_t evals = fresh ? 0 : st->evals64;
-  const double ly = H[1 * D + 1];
-  const double gamma_term = fabs(H[0 * D + 1] - g.tilt_b) / ly * A.rlist;
+  int64_t evals32 = fresh ? 0 : st->evals32;
+  const int64_t iters0 = iters;
+  const double gamma_term = fabs(H[0 * D + 1] - g.tilt_b) / H[1 * D + 1] * A.rlist;
   const double vol = D == 2 ? H[0] * H[3] : H[0] * H[4] * H[8];
+  bool want_e = MIXED;  // mixed: every FP64 evaluation also gives E and tau
+  double wmax = 0.0;    // max |x_ref - x_b| at the last FP64 evaluation (mixed)
+  int status = kStatusRunning;
+  double E = 0.0, W = 0.0, fmx = 0.0;
 
   int ty[APT];
-  float q32[APT][3];
+  float q32[APT][3], d32[APT][3], v32[APT][3], fr32[APT][3];
 #pragma unroll
   for (int k = 0; k < APT; k++) {
     int li = tid + k * nthr;
     ty[k] = 0;
+#pragma unroll
+    for (int c = 0; c < 3; c++) q32[k][c] = d32[k][c] = v32[k][c] = fr32[k][c] = 0.0f;
     if (li < cnt) {
       int64_t gi = base + li;
       ty[k] = A.type[gi];
-      if (fresh) {
-        for (int c = 0; c < D; c++) {
+      for (int c = 0; c < D; c++) {
+        if (fresh) {
           A.v[c * N + gi] = 0.0;
           A.xs[c * N + gi] = A.x[c * N + gi];
         }
+        if (MIXED) v32[k][c] = (float)A.v[c * N + gi];
       }
-      if (MIXED)
-        for (int c = 0; c < D; c++) A.dl[c * N + gi] = 0.0;
+      if (LSM) {
+        const int nn = A.nnb[gi];
+        const uint32_t* row = A.nb + g.nb_off + lo + li;
+        for (int j = 0; j < nn; j++) lst[j * lstride + li] = __ldg(row + (int64_t)j * n);
+      }
     }
   }
-  // publish FP64 positions for the first (always FP64) evaluation
   auto publish64 = [&](int k) {
     int li = tid + k * nthr;
     int64_t gi = base + li;
@@ -265,35 +285,34 @@ __global__ void __launch_bounds__(1024, 1) k_minimize(MinArgs A) {
 #pragma unroll
   for (int k = 0; k < APT; k++)
     if (tid + k * nthr < cnt) publish64(k);
-  cl.sync();
-
   int mode = kModeEval64;
-  bool want_e = MIXED;  // mixed: every FP64 evaluation also gives E and tau
-  double wmax = 0.0;    // max |x_ref - x_b| at the last FP64 evaluation (mixed)
-  int status = kStatusRunning;
-  double E = 0.0, W = 0.0, fmx = 0.0;
+  cl.sync();
 
   for (;;) {
     // ================= force phase =================
     double r[kNumRed];
 #pragma unroll
     for (int m = 0; m < kNumRed; m++) r[m] = 0.0;
-    double F[APT][3];
+    double F[APT][3];  // FP64 mode / FP64 evaluations
+    float Fu[APT][3];  // mixed: force used by the FP32 update
 #pragma unroll
     for (int k = 0; k < APT; k++) {
-      for (int c = 0; c < 3; c++) F[k][c] = 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        F[k][c] = 0.0;
+        Fu[k][c] = 0.0f;
+      }
       int li = tid + k * nthr;
       if (li >= cnt) continue;
       int64_t gi = base + li;
-      int il = lo + li;  // replica-local index
-      const uint32_t* row = A.nb + g.nb_off + il;
+      const uint32_t* row = A.nb + g.nb_off + lo + li;
       const int nn = A.nnb[gi];
       const int ti = ty[k];
       if (mode == kModeEval64) {
         double qi[3], e = 0.0, w = 0.0;
         load_pub64<D>(&pub[li], qi);
         for (int j = 0; j < nn; j++) {
-          uint32_t ent = __ldg(row + (int64_t)j * n);
+          uint32_t ent = LSM ? lst[j * lstride + li] : __ldg(row + (int64_t)j * n);
           double qj[3], d[3];
           load_pub64<D>(rpub[nb_owner(ent)] + nb_slot(ent), qj);
           const double* of = off64 + 3 * nb_code(ent);
@@ -303,18 +322,34 @@ __global__ void __launch_bounds__(1024, 1) k_minimize(MinArgs A) {
         }
         r[6] += e;
         r[7] += w;
+        double f2 = 0.0, pv = 0.0, v2 = 0.0, u2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; c++) {
+          double vc = MIXED ? (double)v32[k][c] : A.v[c * N + gi];
+          f2 = fma(F[k][c], F[k][c], f2);
+          pv = fma(F[k][c], vc, pv);
+          v2 = fma(vc, vc, v2);
+          double u = A.x[c * N + gi] - A.xb[c * N + gi];
+          u2 = fma(u, u, u2);
+        }
         if (MIXED) {
 #pragma unroll
           for (int c = 0; c < D; c++) {
-            A.fref[c * N + gi] = F[k][c];
+            fr32[k][c] = (float)F[k][c];
+            Fu[k][c] = fr32[k][c];
             q32[k][c] = (float)qi[c];
           }
         }
+        r[0] = nmax(r[0], f2);
+        r[1] += pv;
+        r[2] += f2;
+        r[3] += v2;
+        r[5] = nmax(r[5], u2);
       } else {
         float qi[3], di[3], f[3] = {0.f, 0.f, 0.f};
         load_pub32<D>(&pub[li], qi, di);
         for (int j = 0; j < nn; j++) {
-          uint32_t ent = __ldg(row + (int64_t)j * n);
+          uint32_t ent = LSM ? lst[j * lstride + li] : __ldg(row + (int64_t)j * n);
           float qj[3], dj[3], d0[3], e[3];
           load_pub32<D>(rpub[nb_owner(ent)] + nb_slot(ent), qj, dj);
           const float* of = off32 + 3 * nb_code(ent);
@@ -325,40 +360,24 @@ __global__ void __launch_bounds__(1024, 1) k_minimize(MinArgs A) {
           }
           pair_dev<D>(coef[ti * A.nt + nb_type(ent)], d0, e, f);
         }
-#pragma unroll
-        for (int c = 0; c < D; c++) F[k][c] = A.fref[c * N + gi] + (double)f[c];
-      }
-      // per-atom contributions to the FIRE reductions
-      double f2 = 0.0, pv = 0.0, v2 = 0.0, u2 = 0.0, d2 = 0.0;
-#pragma unroll
-      for (int c = 0; c < D; c++) {
-        double vc = A.v[c * N + gi];
-        f2 = fma(F[k][c], F[k][c], f2);
-        pv = fma(F[k][c], vc, pv);
-        v2 = fma(vc, vc, v2);
-      }
-      if (!MIXED || mode == kModeEval64) {
+        float f2 = 0.f, pv = 0.f, v2 = 0.f, dd = 0.f;
 #pragma unroll
         for (int c = 0; c < D; c++) {
-          double u = A.x[c * N + gi] - A.xb[c * N + gi];
-          u2 = fma(u, u, u2);
+          Fu[k][c] = fr32[k][c] + f[c];
+          f2 = fmaf(Fu[k][c], Fu[k][c], f2);
+          pv = fmaf(Fu[k][c], v32[k][c], pv);
+          v2 = fmaf(v32[k][c], v32[k][c], v2);
+          dd = fmaf(d32[k][c], d32[k][c], dd);
         }
-      } else {
-#pragma unroll
-        for (int c = 0; c < D; c++) {
-          double dd = A.dl[c * N + gi];
-          d2 = fma(dd, dd, d2);
-        }
+        r[0] = nmax(r[0], (double)f2);
+        r[1] += (double)pv;
+        r[2] += (double)f2;
+        r[3] += (double)v2;
+        r[4] = nmax(r[4], (double)dd);
       }
-      r[0] = nmax(r[0], f2);
-      r[1] += pv;
-      r[2] += f2;
-      r[3] += v2;
-      r[4] = nmax(r[4], d2);
-      r[5] = nmax(r[5], u2);
     }
 
-    // ================= reduction =================
+    // ================= reduction (FP64, fixed order) =================
 #pragma unroll
     for (int m = 0; m < kNumRed; m++) {
 #pragma unroll
@@ -384,6 +403,7 @@ __global__ void __launch_bounds__(1024, 1) k_minimize(MinArgs A) {
     }
     cl.sync();  // (A) partials of every CTA visible; all force phases done
     if (warp == 0) {
+      double T[kNumRed];
 #pragma unroll
       for (int m = 0; m < kNumRed; m++) {
         double t = lane < C ? rred[lane][m] : 0.0;
@@ -392,137 +412,162 @@ __global__ void __launch_bounds__(1024, 1) k_minimize(MinArgs A) {
           double u = __shfl_xor_sync(0xffffffffu, t, o);
           t = is_max_slot(m) ? nmax(t, u) : t + u;
         }
-        if (lane == 0) tot[m] = t;
+        T[m] = t;
+      }
+      // ================= decisions (thread 0; identical in every CTA) ====
+      if (lane == 0) {
+        const bool was64 = mode == kModeEval64;
+        if (was64) evals++;
+        else evals32++;
+        fmx = sqrt(T[0]);
+        const bool finite = (T[0] < INFINITY) && (T[2] < INFINITY) && (T[1] == T[1]) &&
+                            (!was64 || !want_e || (fabs(T[6]) < INFINITY));
+        double umax;
+        if (!MIXED || was64) {
+          umax = sqrt(T[5]);
+          if (MIXED) wmax = umax;
+        } else {
+          umax = wmax + sqrt(T[4]);
+        }
+        int next = -1;  // -1: FIRE move; else no-move re-evaluation in that mode
+        bool stop = false;
+        if (2.0 * umax + gamma_term > A.skin) {
+          status = kStatusRebuild;  // forces of this pass may miss pairs: discard
+          stop = true;
+        } else if (!finite) {
+          if (MIXED && !was64) next = kModeEval64;
+          else { status = AQS_ERR_NONFINITE; stop = true; }
+        } else if (was64 && fmx < fp.tol) {
+          if (want_e) {
+            E = 0.5 * T[6];
+            W = 0.5 * T[7] / vol;
+            status = AQS_OK;
+            stop = true;
+          } else {
+            want_e = true;  // one more FP64 pass at the same positions for E and tau
+            next = kModeEval64;
+          }
+        } else if (MIXED && !was64 &&
+                   (fmx < fp.tol || sqrt(T[4]) > fmin(fp.ref_ratio * fmx, fp.ref_dmax))) {
+          next = kModeEval64;  // new FP64 reference at the current positions
+        } else if (iters >= fp.max_iter) {
+          status = AQS_ERR_NOT_CONVERGED;
+          stop = true;
+        } else if (iters - iters0 >= A.launch_budget) {
+          stop = true;  // status stays "running": the next launch resumes
+        }
+        Ctl c;
+        c.stop = stop;
+        c.move = !stop && next < 0;
+        c.reset = 0;
+        c.dt = dt;
+        c.ratio = 0.0;
+        c.keep = 1.0;
+        if (c.move) {
+          const double P = T[1], F2 = T[2], V2 = T[3];
+          if (P >= 0.0) {
+            npos++;
+            if (npos > fp.n_min) {
+              dt = fmin(dt * fp.f_inc, fp.dt_max);
+              alpha *= fp.f_alpha;
+            }
+          } else {
+            npos = 0;
+            dt = fmax(dt * fp.f_dec, fp.dt_min);
+            alpha = fp.alpha0;
+            c.reset = 1;
+          }
+          // |v + dt F| after the Euler step, from the reductions already made
+          const double vn2 = c.reset ? dt * dt * F2 : V2 + 2.0 * dt * P + dt * dt * F2;
+          c.dt = dt;
+          c.ratio = alpha * sqrt(vn2 / F2);
+          c.keep = 1.0 - alpha;
+          iters++;
+          mode = MIXED ? kModeDev : kModeEval64;
+        } else if (!stop) {
+          mode = kModeEval64;
+        }
+        c.mode = mode;
+        ctl = c;
       }
     }
     __syncthreads();
-    double T[kNumRed];
-#pragma unroll
-    for (int m = 0; m < kNumRed; m++) T[m] = tot[m];
+    const Ctl c = ctl;
+    mode = c.mode;
+    if (c.stop) break;
 
-    // ================= uniform decisions =================
-    const bool was64 = mode == kModeEval64;
-    if (was64) evals++;
-    fmx = sqrt(T[0]);
-    const bool finite = (T[0] < INFINITY) && (T[2] < INFINITY) && (T[1] == T[1]) &&
-                        (!was64 || !want_e || (T[6] == T[6] && fabs(T[6]) < INFINITY));
-    double umax;
-    if (!MIXED || was64) {
-      umax = sqrt(T[5]);
-      if (MIXED) wmax = umax;
-    } else {
-      umax = wmax + sqrt(T[4]);
-    }
-    int next = -1;  // -1: FIRE move; otherwise the mode of a no-move re-evaluation
-    bool stop = false;
-    if (2.0 * umax + gamma_term > A.skin) {
-      status = kStatusRebuild;  // forces of this pass may miss pairs: discard
-      stop = true;
-    } else if (!finite) {
-      if (MIXED && !was64) next = kModeEval64;
-      else { status = AQS_ERR_NONFINITE; stop = true; }
-    } else if (was64 && fmx < fp.tol) {
-      if (want_e) {
-        E = 0.5 * T[6];
-        W = 0.5 * T[7] / vol;
-        status = AQS_OK;
-        stop = true;
-      } else {
-        want_e = true;  // one more FP64 pass at the same positions for E and tau
-        next = kModeEval64;
-      }
-    } else if (MIXED && !was64 &&
-               (fmx < fp.tol || sqrt(T[4]) > fmin(fp.ref_ratio * fmx, fp.ref_dmax))) {
-      next = kModeEval64;  // new FP64 reference at the current positions
-    } else if (iters >= fp.max_iter) {
-      status = AQS_ERR_NOT_CONVERGED;
-      stop = true;
-    }
-    if (stop) break;
-
-    if (next < 0) {
+    if (c.move) {
       // ================= FIRE update =================
-      const double P = T[1], F2 = T[2], V2 = T[3];
-      bool reset;
-      if (P >= 0.0) {
-        npos++;
-        if (npos > fp.n_min) {
-          dt = fmin(dt * fp.f_inc, fp.dt_max);
-          alpha *= fp.f_alpha;
-        }
-        reset = false;
-      } else {
-        npos = 0;
-        dt = fmax(dt * fp.f_dec, fp.dt_min);
-        alpha = fp.alpha0;
-        reset = true;
-      }
-      // |v + dt F| after the Euler step, from the reductions already made
-      const double vn2 = reset ? dt * dt * F2 : V2 + 2.0 * dt * P + dt * dt * F2;
-      const double ratio = alpha * sqrt(vn2) / sqrt(F2);
-      const double keep = 1.0 - alpha;
+      if (MIXED) {
+        const float dtf = (float)c.dt, kf = (float)c.keep, rf = (float)c.ratio;
+        const float ms = (float)fp.max_step;
 #pragma unroll
-      for (int k = 0; k < APT; k++) {
-        int li = tid + k * nthr;
-        if (li >= cnt) continue;
-        int64_t gi = base + li;
-        double s[3], len2 = 0.0;
+        for (int k = 0; k < APT; k++) {
+          int li = tid + k * nthr;
+          if (li >= cnt) continue;
+          float s[3], len2 = 0.f;
 #pragma unroll
-        for (int c = 0; c < D; c++) {
-          double vc = reset ? 0.0 : A.v[c * N + gi];
-          vc = fma(keep, fma(dt, F[k][c], vc), ratio * F[k][c]);
-          A.v[c * N + gi] = vc;
-          s[c] = dt * vc;
-          len2 = fma(s[c], s[c], len2);
-        }
-        double scale = len2 > fp.max_step * fp.max_step ? fp.max_step / sqrt(len2) : 1.0;
-        if (MIXED) {
-          float dd[3];
-#pragma unroll
-          for (int c = 0; c < D; c++) {
-            double nd = fma(scale, s[c], A.dl[c * N + gi]);
-            A.dl[c * N + gi] = nd;
-            dd[c] = (float)nd;
+          for (int cc = 0; cc < D; cc++) {
+            float vc = c.reset ? 0.0f : v32[k][cc];
+            vc = fmaf(kf, fmaf(dtf, Fu[k][cc], vc), rf * Fu[k][cc]);
+            v32[k][cc] = vc;
+            s[cc] = dtf * vc;
+            len2 = fmaf(s[cc], s[cc], len2);
           }
-          store_pub32<D>(&pub[li], q32[k], dd);
-        } else {
+          float scale = len2 > ms * ms ? ms * rsqrtf(len2) : 1.0f;
 #pragma unroll
-          for (int c = 0; c < D; c++) A.x[c * N + gi] = fma(scale, s[c], A.x[c * N + gi]);
-          publish64(k);
+          for (int cc = 0; cc < D; cc++) d32[k][cc] = fmaf(scale, s[cc], d32[k][cc]);
+          store_pub32<D>(&pub[li], q32[k], d32[k]);
         }
-      }
-      iters++;
-      mode = MIXED ? kModeDev : kModeEval64;
-    } else {
-      // no move: re-evaluate in FP64 at the current positions
-      if (MIXED && !was64) {
+      } else {
+        const double cdt = c.dt, keep = c.keep, ratio = c.ratio;
 #pragma unroll
         for (int k = 0; k < APT; k++) {
           int li = tid + k * nthr;
           if (li >= cnt) continue;
           int64_t gi = base + li;
-          for (int c = 0; c < D; c++) {
-            A.x[c * N + gi] += A.dl[c * N + gi];
-            A.dl[c * N + gi] = 0.0;
+          double s[3], len2 = 0.0;
+#pragma unroll
+          for (int cc = 0; cc < D; cc++) {
+            double vc = c.reset ? 0.0 : A.v[cc * N + gi];
+            vc = fma(keep, fma(cdt, F[k][cc], vc), ratio * F[k][cc]);
+            A.v[cc * N + gi] = vc;
+            s[cc] = cdt * vc;
+            len2 = fma(s[cc], s[cc], len2);
           }
+          double scale = len2 > fp.max_step * fp.max_step ? fp.max_step / sqrt(len2) : 1.0;
+#pragma unroll
+          for (int cc = 0; cc < D; cc++) A.x[cc * N + gi] = fma(scale, s[cc], A.x[cc * N + gi]);
           publish64(k);
         }
       }
-      mode = kModeEval64;
+    } else if (MIXED && c.mode == kModeEval64) {
+      // no move: fold delta into the reference and publish FP64 positions
+#pragma unroll
+      for (int k = 0; k < APT; k++) {
+        int li = tid + k * nthr;
+        if (li >= cnt) continue;
+        int64_t gi = base + li;
+        for (int cc = 0; cc < D; cc++) {
+          A.x[cc * N + gi] += (double)d32[k][cc];
+          d32[k][cc] = 0.0f;
+        }
+        publish64(k);
+      }
     }
     cl.sync();  // (B) new positions visible; partial slots free again
   }
 
-  // ---- exit: materialise x = x_ref + delta, store the FIRE state ----
+  // ---- exit: materialise x = x_ref + delta, keep v, store the FIRE state ----
   if (MIXED) {
 #pragma unroll
     for (int k = 0; k < APT; k++) {
       int li = tid + k * nthr;
       if (li >= cnt) continue;
       int64_t gi = base + li;
-      for (int c = 0; c < D; c++) {
-        A.x[c * N + gi] += A.dl[c * N + gi];
-        A.dl[c * N + gi] = 0.0;
+      for (int cc = 0; cc < D; cc++) {
+        A.x[cc * N + gi] += (double)d32[k][cc];
+        A.v[cc * N + gi] = (double)v32[k][cc];
       }
     }
   }
@@ -532,6 +577,7 @@ __global__ void __launch_bounds__(1024, 1) k_minimize(MinArgs A) {
     st->npos = npos;
     st->iters = iters;
     st->evals64 = evals;
+    st->evals32 = evals32;
     st->status = status;
     st->fmax = fmx;
     st->fresh = 0;
@@ -544,17 +590,21 @@ __global__ void __launch_bounds__(1024, 1) k_minimize(MinArgs A) {
 }
 
 // ---------------------------------------------------------------- launcher
-size_t minimize_smem_bytes(int dim, int npc, int nt) {
-  size_t pub = (dim == 2 ? sizeof(Pub<2>) : sizeof(Pub<3>)) * (size_t)npc;
-  size_t rest = sizeof(double) * (kNumRed * 34 + 27 * 3) + sizeof(float) * (27 * 3 + 3) +
-                sizeof(PairCoef) * nt * nt + 64;
-  return pub + rest;
+static size_t smem_fixed(int dim, int nt) {
+  (void)dim;
+  return sizeof(double) * (kNumRed * 33 + 27 * 3) + sizeof(float) * (27 * 3 + 3) +
+         sizeof(PairCoef) * nt * nt + 64;
 }
 
-template <int D, bool MIXED, int APT>
+size_t minimize_smem_bytes(int dim, int npc, int nt, int cap, bool list_in_smem) {
+  size_t pub = (dim == 2 ? sizeof(Pub<2>) : sizeof(Pub<3>)) * (size_t)npc;
+  return pub + smem_fixed(dim, nt) + (list_in_smem ? sizeof(uint32_t) * (size_t)cap * npc : 0);
+}
+
+template <int D, bool MIXED, int APT, bool LSM>
 static cudaError_t launch_t(const MinArgs& a, int n_clusters, int C, int threads, size_t smem,
                             cudaStream_t s) {
-  auto kern = k_minimize<D, MIXED, APT>;
+  auto kern = k_minimize<D, MIXED, APT, LSM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (C > 8) {
@@ -577,28 +627,37 @@ static cudaError_t launch_t(const MinArgs& a, int n_clusters, int C, int threads
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <int D, bool MIXED>
+template <int D, bool MIXED, bool LSM>
 static cudaError_t launch_apt(const MinArgs& a, int n_clusters, int C, int npc, size_t smem,
                               cudaStream_t s) {
-  int apt = npc <= 1024 ? 1 : (npc <= 2048 ? 2 : 4);
+  int apt = npc <= 512 ? 1 : (npc <= 1024 ? 2 : (npc <= 2048 ? 4 : 8));
   int threads = (npc + apt - 1) / apt;
   threads = ((threads + 31) / 32) * 32;
-  if (threads > 1024) return cudaErrorInvalidValue;
+  if (threads > 512) return cudaErrorInvalidValue;
   switch (apt) {
-    case 1: return launch_t<D, MIXED, 1>(a, n_clusters, C, threads, smem, s);
-    case 2: return launch_t<D, MIXED, 2>(a, n_clusters, C, threads, smem, s);
-    default: return launch_t<D, MIXED, 4>(a, n_clusters, C, threads, smem, s);
+    case 1: return launch_t<D, MIXED, 1, LSM>(a, n_clusters, C, threads, smem, s);
+    case 2: return launch_t<D, MIXED, 2, LSM>(a, n_clusters, C, threads, smem, s);
+    case 4: return launch_t<D, MIXED, 4, LSM>(a, n_clusters, C, threads, smem, s);
+    default: return launch_t<D, MIXED, 8, LSM>(a, n_clusters, C, threads, smem, s);
   }
 }
 
-cudaError_t launch_minimize(int dim, bool mixed, const MinArgs& a, int n_clusters, int C, int npc,
-                            cudaStream_t s) {
-  size_t smem = minimize_smem_bytes(dim, npc, a.nt);
-  if (dim == 2)
-    return mixed ? launch_apt<2, true>(a, n_clusters, C, npc, smem, s)
-                 : launch_apt<2, false>(a, n_clusters, C, npc, smem, s);
-  return mixed ? launch_apt<3, true>(a, n_clusters, C, npc, smem, s)
-               : launch_apt<3, false>(a, n_clusters, C, npc, smem, s);
+cudaError_t launch_minimize(int dim, bool mixed, MinArgs a, int n_clusters, int C, int npc,
+                            int cap, cudaStream_t s) {
+  a.npc_launch = npc;
+  const size_t limit = 220 * 1024;
+  bool lsm = minimize_smem_bytes(dim, npc, a.nt, cap, true) <= limit;
+  size_t smem = minimize_smem_bytes(dim, npc, a.nt, cap, lsm);
+  if (dim == 2) {
+    if (mixed) return lsm ? launch_apt<2, true, true>(a, n_clusters, C, npc, smem, s)
+                          : launch_apt<2, true, false>(a, n_clusters, C, npc, smem, s);
+    return lsm ? launch_apt<2, false, true>(a, n_clusters, C, npc, smem, s)
+               : launch_apt<2, false, false>(a, n_clusters, C, npc, smem, s);
+  }
+  if (mixed) return lsm ? launch_apt<3, true, true>(a, n_clusters, C, npc, smem, s)
+                        : launch_apt<3, true, false>(a, n_clusters, C, npc, smem, s);
+  return lsm ? launch_apt<3, false, true>(a, n_clusters, C, npc, smem, s)
+             : launch_apt<3, false, false>(a, n_clusters, C, npc, smem, s);
 }
 
 }  // namespace aqs

@@ -23,10 +23,12 @@ struct MinArgs {
   int nt;
   FireDev fire;
   double skin, rlist;
+  int64_t launch_budget;  // FIRE iterations per launch before yielding
+  int npc_launch;         // shared-memory stride (largest npc of the launch)
 };
 
-size_t minimize_smem_bytes(int dim, int npc, int nt);
-cudaError_t launch_minimize(int dim, bool mixed, const MinArgs& a, int n_clusters, int C, int npc,
-                            cudaStream_t s);
+size_t minimize_smem_bytes(int dim, int npc, int nt, int cap, bool list_in_smem);
+cudaError_t launch_minimize(int dim, bool mixed, MinArgs a, int n_clusters, int C, int npc,
+                            int cap, cudaStream_t s);
 
 }  // namespace aqs

@@ -22,6 +22,8 @@ namespace aqs {
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 static thread_local std::string g_err;
+static std::atomic<int> g_timing{0};
+static aqs_kernel_stats g_stats{};
 
 static aqs_status fail(aqs_status s, const char* fmt, ...) {
   char buf[512];
@@ -66,6 +68,9 @@ struct aqs_system {
   std::vector<RepGeom> geom;
   std::vector<RepState> st;
   std::vector<double> mean_nb;
+  std::vector<int64_t> nnb_sum;
+  int64_t* d_nnbsum = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   PairCoef coef[AQS_MAX_TYPES * AQS_MAX_TYPES];
   float rl2f[AQS_MAX_TYPES * AQS_MAX_TYPES];
   int total_cells = 0, cells_cap = 0;
@@ -278,10 +283,16 @@ aqs_status rebuild(aqs_system* s, const std::vector<uint8_t>& flags, int depth =
     CUDA_TRY(launch_rebuild_bin(D, a, s->R, s->stream));
     CUDA_TRY(launch_rebuild_sort(D, a, total, s->stream));
     CUDA_TRY(launch_rebuild_verlet(D, a, s->stream));
+    CUDA_TRY(launch_sum_nnb(a, s->R, s->d_nnbsum, s->stream));
     std::vector<int32_t> over(s->R);
+    std::vector<int64_t> sums(s->R);
     CUDA_TRY(cudaMemcpyAsync(over.data(), s->overflow, sizeof(int32_t) * s->R,
                              cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(sums.data(), s->d_nnbsum, sizeof(int64_t) * s->R,
+                             cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
+    for (int r = 0; r < s->R; r++)
+      if (flags[r]) s->nnb_sum[r] = sums[r];
     int need = 0;
     for (int r = 0; r < s->R; r++) need = std::max(need, over[r]);
     if (need > 0) {
@@ -369,6 +380,8 @@ MinArgs min_args(aqs_system* s, const aqs_fire_params* f) {
   a.fire = fire_dev(f);
   a.skin = s->skin;
   a.rlist = s->rlist;
+  a.launch_budget = 4096;
+  a.npc_launch = 0;
   return a;
 }
 
@@ -412,7 +425,7 @@ aqs_status minimize_impl(aqs_system* s, const aqs_fire_params* f, const std::vec
   AQS_TRY(upload_state(s));
   std::vector<int64_t> rebuilds(s->R, 0);
   std::vector<int> order_work;
-  for (int pass = 0; pass < 100000 && !todo.empty(); pass++) {
+  for (int64_t pass = 0; pass < 10000000 && !todo.empty(); pass++) {
     // group the pending replicas by cluster size; one launch per group
     std::vector<int> Cs;
     for (int r : todo) Cs.push_back(s->geom[r].C);
@@ -429,6 +442,11 @@ aqs_status minimize_impl(aqs_system* s, const aqs_fire_params* f, const std::vec
     CUDA_TRY(cudaMemcpyAsync(s->d_work, order_work.data(), sizeof(int) * order_work.size(),
                              cudaMemcpyHostToDevice, s->stream));
     MinArgs a = min_args(s, f);
+    const bool timing = g_timing.load() != 0;
+    std::vector<RepState> before(s->st);
+    for (int r : todo)
+      if (s->st[r].fresh) before[r].evals32 = before[r].evals64 = before[r].iters = 0;
+    if (timing) CUDA_TRY(cudaEventRecord(s->ev0, s->stream));
     for (size_t gi = 0; gi < groups.size(); gi++) {
       int C = Cs[gi];
       int npc = 0;
@@ -436,17 +454,34 @@ aqs_status minimize_impl(aqs_system* s, const aqs_fire_params* f, const std::vec
         npc = std::max(npc, s->geom[order_work[groups[gi].first + k]].npc);
       a.work = s->d_work + groups[gi].first;
       CUDA_TRY(launch_minimize(s->dim, s->prec == AQS_MIXED, a, groups[gi].second, C, npc,
-                               s->stream));
+                               s->cap, s->stream));
     }
+    if (timing) CUDA_TRY(cudaEventRecord(s->ev1, s->stream));
     AQS_TRY(download_state(s));
+    if (timing) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+      g_stats.launches += (int64_t)groups.size();
+      g_stats.kernel_ms += ms;
+      for (int r : todo) {
+        int64_t d32 = s->st[r].evals32 - before[r].evals32;
+        int64_t d64 = s->st[r].evals64 - before[r].evals64;
+        g_stats.evals32 += d32;
+        g_stats.evals64 += d64;
+        g_stats.pairs32 += d32 * s->nnb_sum[r];
+        g_stats.pairs64 += d64 * s->nnb_sum[r];
+        g_stats.atom_iters += (s->st[r].iters - before[r].iters) * s->n[r];
+      }
+    }
     std::vector<uint8_t> flags(s->R, 0);
     std::vector<int> next;
-    for (int r : todo)
+    for (int r : todo) {
       if (s->st[r].status == kStatusRebuild) {
         flags[r] = 1;
-        next.push_back(r);
         rebuilds[r]++;
       }
+      if (s->st[r].status == kStatusRebuild || s->st[r].status == kStatusRunning) next.push_back(r);
+    }
     if (!next.empty()) AQS_TRY(rebuild(s, flags));
     todo.swap(next);
   }
@@ -529,6 +564,9 @@ aqs_status alloc_system(aqs_system* s) {
   AQS_TRY(alloc_arr(s, &s->d_partial, 2 * (energy_blocks((int)s->nmax) + 1)));
   AQS_TRY(alloc_arr(s, &s->d_i64, 4 * std::max(s->R, 64)));
   AQS_TRY(alloc_arr(s, &s->d_shift, std::max(s->R, 64)));
+  AQS_TRY(alloc_arr(s, &s->d_nnbsum, s->R));
+  CUDA_TRY(cudaEventCreate(&s->ev0));
+  CUDA_TRY(cudaEventCreate(&s->ev1));
   CUDA_TRY(cudaMemsetAsync(s->v, 0, sizeof(double) * D * N, s->stream));
   CUDA_TRY(cudaMemsetAsync(s->dl, 0, sizeof(double) * D * N, s->stream));
   CUDA_TRY(cudaMemsetAsync(s->fref, 0, sizeof(double) * D * N, s->stream));
@@ -565,6 +603,7 @@ aqs_status init_system(aqs_system* s, int dim, int R, const int64_t* n, const aq
   s->geom.assign(R, RepGeom{});
   s->st.assign(R, RepState{});
   s->mean_nb.assign(R, 0.0);
+  s->nnb_sum.assign(R, 0);
   for (int r = 0; r < R; r++) {
     RepGeom& g = s->geom[r];
     g.off = s->off[r];
@@ -643,6 +682,8 @@ void destroy(aqs_system* s) {
   if (!s) return;
   if (s->chains) destroy(s->chains);
   cudaStreamSynchronize(s->stream);
+  if (s->ev0) cudaEventDestroy(s->ev0);
+  if (s->ev1) cudaEventDestroy(s->ev1);
   for (auto& a : s->allocs) {
     if (s->ufree) s->ufree(a.p, s->actx);
     else cudaFree(a.p);
@@ -1130,6 +1171,11 @@ aqs_status aqs_energy_forces(aqs_system* s, int r, double* energy, double* force
 }
 
 const char* aqs_last_error(void) { return g_err.c_str(); }
+void aqs_set_kernel_timing(int on) { g_timing.store(on ? 1 : 0); }
+void aqs_get_kernel_stats(aqs_kernel_stats* out) {
+  if (out) *out = g_stats;
+}
+void aqs_reset_kernel_stats(void) { g_stats = aqs_kernel_stats{}; }
 int64_t aqs_launch_count(void) { return g_launches.load(); }
 
 double aqs_mean_neighbours(const aqs_system* s, int r) {
