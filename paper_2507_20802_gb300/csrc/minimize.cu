@@ -182,8 +182,12 @@ constexpr int kModeEval64 = 0, kModeDev = 1;
 // compute it from bitwise identical totals) and read by the CTA's threads.
 struct Ctl {
   double dt, ratio, keep;
-  int move, mode, stop, reset;
+  int move, mode, stop, reset, want_e, was64;
 };
+
+// While the largest FP64 force exceeds this, mixed mode keeps evaluating in
+// FP64 (random starts and collisions), where FP32 would overflow.
+constexpr double kBigForce = 1e3;
 
 template <int D, bool MIXED, int APT, bool LSM>
 __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
@@ -483,40 +487,77 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
           c.ratio = alpha * sqrt(vn2 / F2);
           c.keep = 1.0 - alpha;
           iters++;
-          mode = MIXED ? kModeDev : kModeEval64;
+          mode = (MIXED && !(was64 && fmx > kBigForce)) ? kModeDev : kModeEval64;
         } else if (!stop) {
           mode = kModeEval64;
         }
         c.mode = mode;
+        c.want_e = want_e;
+        c.was64 = was64;
         ctl = c;
       }
     }
     __syncthreads();
     const Ctl c = ctl;
     mode = c.mode;
+    want_e = c.want_e;
     if (c.stop) break;
 
     if (c.move) {
       // ================= FIRE update =================
-      if (MIXED) {
+      if (MIXED && c.was64) {
+        // step after an FP64 evaluation: FP64 arithmetic (forces may be huge)
+#pragma unroll
+        for (int k = 0; k < APT; k++) {
+          int li = tid + k * nthr;
+          if (li >= cnt) continue;
+          double sv[3], mx = 0.0;
+#pragma unroll
+          for (int cc = 0; cc < D; cc++) {
+            double vc = c.reset ? 0.0 : (double)v32[k][cc];
+            vc = fma(c.keep, fma(c.dt, F[k][cc], vc), c.ratio * F[k][cc]);
+            v32[k][cc] = (float)vc;
+            sv[cc] = c.dt * vc;
+            mx = fmax(mx, fabs(sv[cc]));
+          }
+          double scale = 1.0;
+          if (mx > 0.5 * fp.max_step) {
+            double l2 = 0.0;
+#pragma unroll
+            for (int cc = 0; cc < D; cc++) l2 += (sv[cc] / mx) * (sv[cc] / mx);
+            double len = mx * sqrt(l2);
+            if (len > fp.max_step) scale = fp.max_step / len;
+          }
+#pragma unroll
+          for (int cc = 0; cc < D; cc++) d32[k][cc] = (float)((double)d32[k][cc] + scale * sv[cc]);
+          store_pub32<D>(&pub[li], q32[k], d32[k]);
+        }
+      } else if (MIXED) {
         const float dtf = (float)c.dt, kf = (float)c.keep, rf = (float)c.ratio;
         const float ms = (float)fp.max_step;
 #pragma unroll
         for (int k = 0; k < APT; k++) {
           int li = tid + k * nthr;
           if (li >= cnt) continue;
-          float s[3], len2 = 0.f;
+          float sv[3], mx = 0.0f;
 #pragma unroll
           for (int cc = 0; cc < D; cc++) {
             float vc = c.reset ? 0.0f : v32[k][cc];
             vc = fmaf(kf, fmaf(dtf, Fu[k][cc], vc), rf * Fu[k][cc]);
             v32[k][cc] = vc;
-            s[cc] = dtf * vc;
-            len2 = fmaf(s[cc], s[cc], len2);
+            sv[cc] = dtf * vc;
+            mx = fmaxf(mx, fabsf(sv[cc]));
           }
-          float scale = len2 > ms * ms ? ms * rsqrtf(len2) : 1.0f;
+          float scale = 1.0f;
+          if (mx > 0.5f * ms) {
+            float l2 = 0.0f;
 #pragma unroll
-          for (int cc = 0; cc < D; cc++) d32[k][cc] = fmaf(scale, s[cc], d32[k][cc]);
+            for (int cc = 0; cc < D; cc++) l2 = fmaf(sv[cc] / mx, sv[cc] / mx, l2);
+            float len = mx * sqrtf(l2);
+            if (len > ms) scale = ms / len;
+          }
+#pragma unroll
+          for (int cc = 0; cc < D; cc++) d32[k][cc] = fmaf(scale, sv[cc], d32[k][cc]);
           store_pub32<D>(&pub[li], q32[k], d32[k]);
         }
       } else {
@@ -526,16 +567,23 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
           int li = tid + k * nthr;
           if (li >= cnt) continue;
           int64_t gi = base + li;
-          double s[3], len2 = 0.0;
+          double s[3], mx = 0.0;
 #pragma unroll
           for (int cc = 0; cc < D; cc++) {
             double vc = c.reset ? 0.0 : A.v[cc * N + gi];
             vc = fma(keep, fma(cdt, F[k][cc], vc), ratio * F[k][cc]);
             A.v[cc * N + gi] = vc;
             s[cc] = cdt * vc;
-            len2 = fma(s[cc], s[cc], len2);
+            mx = fmax(mx, fabs(s[cc]));
           }
-          double scale = len2 > fp.max_step * fp.max_step ? fp.max_step / sqrt(len2) : 1.0;
+          double scale = 1.0;
+          if (mx > 0.5 * fp.max_step) {
+            double l2 = 0.0;
+#pragma unroll
+            for (int cc = 0; cc < D; cc++) l2 += (s[cc] / mx) * (s[cc] / mx);
+            double len = mx * sqrt(l2);
+            if (len > fp.max_step) scale = fp.max_step / len;
+          }
 #pragma unroll
           for (int cc = 0; cc < D; cc++) A.x[cc * N + gi] = fma(scale, s[cc], A.x[cc * N + gi]);
           publish64(k);
