@@ -530,7 +530,16 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
           }
 #pragma unroll
           for (int cc = 0; cc < D; cc++) d32[k][cc] = (float)((double)d32[k][cc] + scale * sv[cc]);
-          store_pub32<D>(&pub[li], q32[k], d32[k]);
+          if (c.mode == kModeDev) {
+            store_pub32<D>(&pub[li], q32[k], d32[k]);
+          } else {  // the next evaluation is FP64: fold delta into x and publish it
+            int64_t gi = base + li;
+            for (int cc = 0; cc < D; cc++) {
+              A.x[cc * N + gi] += (double)d32[k][cc];
+              d32[k][cc] = 0.0f;
+            }
+            publish64(k);
+          }
         }
       } else if (MIXED) {
         const float dtf = (float)c.dt, kf = (float)c.keep, rf = (float)c.ratio;
@@ -558,7 +567,16 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
           }
 #pragma unroll
           for (int cc = 0; cc < D; cc++) d32[k][cc] = fmaf(scale, sv[cc], d32[k][cc]);
-          store_pub32<D>(&pub[li], q32[k], d32[k]);
+          if (c.mode == kModeDev) {
+            store_pub32<D>(&pub[li], q32[k], d32[k]);
+          } else {  // the next evaluation is FP64: fold delta into x and publish it
+            int64_t gi = base + li;
+            for (int cc = 0; cc < D; cc++) {
+              A.x[cc * N + gi] += (double)d32[k][cc];
+              d32[k][cc] = 0.0f;
+            }
+            publish64(k);
+          }
         }
       } else {
         const double cdt = c.dt, keep = c.keep, ratio = c.ratio;

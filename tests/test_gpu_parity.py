@@ -235,3 +235,18 @@ def test_full_size_workload_properties(A, syn):
         assert res[r]["status"] == 0
         _, Fr, _ = b.energy_forces(r)
         assert np.sqrt((Fr * Fr).sum(1)).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_quench_from_random_start_converges(A, syn, prec):
+    """Overlapping random starts (forces ~1e16) must be handled in both modes:
+    mixed mode stays on FP64 evaluations while forces are huge."""
+    x, t, H = syn.random_glass_start(1000, 2, seed=11)
+    P = A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED
+    s = make_system(A, syn, x, t, H, P)
+    r = s.minimize(A.fire_params(max_iter=400000))[0]
+    assert r["status"] == 0 and r["fmax"] < 1e-10
+    E, F, _ = s.energy_forces()
+    assert np.sqrt((F * F).sum(1)).max() < 1e-10
+    assert E == pytest.approx(r["E"], rel=1e-12)
+    assert E / len(x) < -2.5  # a bound glass, not an exploded configuration
