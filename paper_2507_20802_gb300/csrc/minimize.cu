@@ -30,700 +30,39 @@
 //                min(ref_ratio * fmax, ref_dmax), and the convergence test
 //                max_a |F_a| < tol is only ever passed on an FP64 evaluation.
 //   FIRE state, positions, reductions and the final test are FP64 in both.
-#include <cooperative_groups.h>
-#include <math.h>
-
-#include "aqs_internal.cuh"
-#include "launch.cuh"
-#include "minimize.cuh"
-
-namespace cg = cooperative_groups;
+#include "minimize_launch.cuh"
 
 namespace aqs {
 
-// NaN-propagating max for the reductions (a NaN anywhere must reach the
-// decision so that every CTA stops together).
-__device__ __forceinline__ double nmax(double a, double b) { return (a != a || a > b) ? a : b; }
-
-// Slots 0, 4, 5 are max-reductions, the others sums.
-__device__ __forceinline__ bool is_max_slot(int m) { return m == 0 || m == 4 || m == 5; }
-
-template <int D>
-__device__ __forceinline__ void pair64(const PairCoef& c, const double* d, double* F, bool want_e,
-                                       double& e, double& w) {
-  double s = d[0] * d[0];
-#pragma unroll
-  for (int k = 1; k < D; k++) s = fma(d[k], d[k], s);
-  if (s < c.rc2) {
-    double u = 1.0 / s;
-    double a = rsqrt(s);
-    double u3 = u * u * u, u4 = u3 * u, u7 = u4 * u3;
-    double phi = fma(c.A, u7, fma(c.B, u4, c.C * a));
-#pragma unroll
-    for (int k = 0; k < D; k++) F[k] = fma(phi, d[k], F[k]);
-    if (want_e) {
-      double r = s * a;
-      e += c.e12 * u3 * u3 - c.e6 * u3 - c.Uc - (r - c.rc) * c.dUc;
-      w = fma(phi * d[0], d[1], w);
-    }
-  }
+size_t minimize_smem_bytes(int dim, int npc, int nrep, int nt, int cap, int mem) {
+  return minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, mem);
 }
 
-// phi(s) in FP32
-__device__ __forceinline__ float phi32(const PairCoef& c, float s) {
-  float a = rsqrtf(s);
-  float u = a * a;
-  float u2 = u * u, u4 = u2 * u2, u7 = u4 * u2 * u;
-  return fmaf(c.Af, u7, fmaf(c.Bf, u4, c.Cf * a));
-}
-
-// Force change of one pair between the reference separation d0 and d0 + e,
-// in FP32, by divided differences (no cancellation between phi(s) and
-// phi(s0)).  With u = 1/s, w = 1/s0, ds = s - s0:
-//   (s^-n - s0^-n) / ds = -u w sum_{k<n} u^k w^(n-1-k)
-//   (s^-1/2 - s0^-1/2) / ds = -(ab)^2 / (a + b),  a = s^-1/2, b = s0^-1/2
-//   dF = phi(s) e + [phi(s) - phi(s0)] d0
-template <int D>
-__device__ __forceinline__ void pair_dev(const PairCoef& c, const float* d0, const float* e,
-                                         float* F) {
-  float s0 = d0[0] * d0[0], ds = e[0] * fmaf(2.0f, d0[0], e[0]);
-#pragma unroll
-  for (int k = 1; k < D; k++) {
-    s0 = fmaf(d0[k], d0[k], s0);
-    ds = fmaf(e[k], fmaf(2.0f, d0[k], e[k]), ds);
-  }
-  float s = s0 + ds;
-  bool in0 = s0 < c.rc2f, in1 = s < c.rc2f;
-  if (in0 && in1) {
-    float a = rsqrtf(s), b = rsqrtf(s0);
-    float u = a * a, w = b * b;
-    float w2 = w * w, w3 = w2 * w, w4 = w2 * w2, w5 = w4 * w, w6 = w3 * w3;
-    float h4 = fmaf(u, fmaf(u, w + u, w2), w3);
-    float h7 = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, w + u, w2), w3), w4), w5), w6);
-    float uw = u * w;
-    float ab = a * b;
-    float dh = -(ab * ab) / (a + b);
-    float u2 = u * u, u4 = u2 * u2, u7 = u4 * u2 * u;
-    float phi = fmaf(c.Af, u7, fmaf(c.Bf, u4, c.Cf * a));
-    float dphi = ds * fmaf(-c.Af * uw, h7, fmaf(-c.Bf * uw, h4, c.Cf * dh));
-#pragma unroll
-    for (int k = 0; k < D; k++) F[k] += fmaf(phi, e[k], dphi * d0[k]);
-  } else if (in1) {
-    float phi = phi32(c, s);
-#pragma unroll
-    for (int k = 0; k < D; k++) F[k] = fmaf(phi, d0[k] + e[k], F[k]);
-  } else if (in0) {
-    float phi = phi32(c, s0);
-#pragma unroll
-    for (int k = 0; k < D; k++) F[k] = fmaf(-phi, d0[k], F[k]);
-  }
-}
-
-// Published record of one atom in shared memory.  EVAL64 reads q64 (FP64
-// position relative to the atom's cell origin); the mixed FP32 path reads
-// (q32, delta32).  The two views alias: each iteration publishes exactly the
-// one the next force phase needs, after every CTA has passed the mid-iteration
-// barrier.
-template <int D>
-struct Pub;
-template <>
-struct Pub<2> {
-  union {
-    double q64[2];
-    float4 p32;  // q.x, q.y, delta.x, delta.y
-  };
-};
-template <>
-struct Pub<3> {
-  union {
-    double q64[4];
-    struct {
-      float4 q32;  // q.x, q.y, q.z, 0
-      float4 d32;  // delta.x, delta.y, delta.z, 0
-    } p;
-  };
-};
-
-template <int D>
-__device__ __forceinline__ void load_pub32(const Pub<D>* p, float* q, float* dd) {
-  if constexpr (D == 2) {
-    float4 a = p->p32;
-    q[0] = a.x; q[1] = a.y; dd[0] = a.z; dd[1] = a.w;
-  } else {
-    float4 a = p->p.q32, b = p->p.d32;
-    q[0] = a.x; q[1] = a.y; q[2] = a.z; dd[0] = b.x; dd[1] = b.y; dd[2] = b.z;
-  }
-}
-
-template <int D>
-__device__ __forceinline__ void store_pub32(Pub<D>* p, const float* q, const float* dd) {
-  if constexpr (D == 2) {
-    p->p32 = make_float4(q[0], q[1], dd[0], dd[1]);
-  } else {
-    p->p.q32 = make_float4(q[0], q[1], q[2], 0.0f);
-    p->p.d32 = make_float4(dd[0], dd[1], dd[2], 0.0f);
-  }
-}
-
-template <int D>
-__device__ __forceinline__ void load_pub64(const Pub<D>* p, double* q) {
-  if constexpr (D == 2) {
-    double2 a = *reinterpret_cast<const double2*>(p->q64);
-    q[0] = a.x; q[1] = a.y;
-  } else {
-    double2 a = *reinterpret_cast<const double2*>(p->q64);
-    q[0] = a.x; q[1] = a.y; q[2] = p->q64[2];
-  }
-}
-
-constexpr int kModeEval64 = 0, kModeDev = 1;
-
-// Control block written once per iteration by thread 0 of every CTA (all CTAs
-// compute it from bitwise identical totals) and read by the CTA's threads.
-struct Ctl {
-  double dt, ratio, keep;
-  int move, mode, stop, reset, want_e, was64;
-};
-
-// While the largest FP64 force exceeds this, mixed mode keeps evaluating in
-// FP64 (random starts and collisions), where FP32 would overflow.
-constexpr double kBigForce = 1e3;
-
-template <int D, bool MIXED, int APT, bool LSM>
-__global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
-  cg::cluster_group cl = cg::this_cluster();
-  const int C = (int)cl.num_blocks();
-  const int rank = (int)cl.block_rank();
-  const int ri = A.work[blockIdx.x / C];
-  const RepGeom& g = A.geom[ri];
-  RepState* st = A.state + ri;
-  const int n = g.n, npc = g.npc;
-  const int lo = rank * npc;
-  const int cnt = max(0, min(npc, n - lo));
-  const int64_t base = g.off + lo;  // global index of local slot 0
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
-  const int64_t N = A.ntot;
-  const int lstride = A.npc_launch;
-
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Pub<D>* pub = reinterpret_cast<Pub<D>*>(smem_raw);
-  double* red = reinterpret_cast<double*>(smem_raw + sizeof(Pub<D>) * lstride);  // [kNumRed]
-  double* wred = red + kNumRed;                                                   // [32][kNumRed]
-  double* off64 = wred + 32 * kNumRed;                                            // [27][3]
-  float* off32 = reinterpret_cast<float*>(off64 + 27 * 3);                        // [27][3]
-  PairCoef* coef = reinterpret_cast<PairCoef*>(off32 + 27 * 3 + 3);               // [nt*nt]
-  uint32_t* lst = reinterpret_cast<uint32_t*>(coef + A.nt * A.nt);                // [cap][lstride]
-  __shared__ Pub<D>* rpub[kMaxCluster];
-  __shared__ double* rred[kMaxCluster];
-  __shared__ Ctl ctl;
-
-  // ---- set-up: tables, remote bases, list rows, FIRE state ----
-  double H[9];
-#pragma unroll
-  for (int k = 0; k < 9; k++) H[k] = g.H[k];
-  const int ncode = D == 2 ? 9 : 27;
-  if (tid < ncode) {
-    double o[3];
-    cell_offset<D>(H, g.nc, tid, o);
-    for (int k = 0; k < D; k++) {
-      off64[tid * 3 + k] = o[k];
-      off32[tid * 3 + k] = (float)o[k];
-    }
-  }
-  for (int k = tid; k < A.nt * A.nt; k += nthr) coef[k] = A.coef[k];
-  if (tid < C) {
-    rpub[tid] = cl.map_shared_rank(pub, tid);
-    rred[tid] = cl.map_shared_rank(red, tid);
-  }
-  const FireDev fp = A.fire;
-  const bool fresh = st->fresh != 0;
-  // FIRE scalars: meaningful in thread 0 only
-  double dt = fresh ? fp.dt0 : st->dt;
-  double alpha = fresh ? fp.alpha0 : st->alpha;
-  int npos = fresh ? 0 : st->npos;
-  int64_t iters = fresh ? 0 : st->iters;
-  int64_t evals = fresh ? 0 : st->evals64;
-  int64_t evals32 = fresh ? 0 : st->evals32;
-  const int64_t iters0 = iters;
-  const double gamma_term = fabs(H[0 * D + 1] - g.tilt_b) / H[1 * D + 1] * A.rlist;
-  const double vol = D == 2 ? H[0] * H[3] : H[0] * H[4] * H[8];
-  bool want_e = MIXED;  // mixed: every FP64 evaluation also gives E and tau
-  double wmax = 0.0;    // max |x_ref - x_b| at the last FP64 evaluation (mixed)
-  int status = kStatusRunning;
-  double E = 0.0, W = 0.0, fmx = 0.0;
-
-  int ty[APT];
-  float q32[APT][3], d32[APT][3], v32[APT][3], fr32[APT][3];
-#pragma unroll
-  for (int k = 0; k < APT; k++) {
-    int li = tid + k * nthr;
-    ty[k] = 0;
-#pragma unroll
-    for (int c = 0; c < 3; c++) q32[k][c] = d32[k][c] = v32[k][c] = fr32[k][c] = 0.0f;
-    if (li < cnt) {
-      int64_t gi = base + li;
-      ty[k] = A.type[gi];
-      for (int c = 0; c < D; c++) {
-        if (fresh) {
-          A.v[c * N + gi] = 0.0;
-          A.xs[c * N + gi] = A.x[c * N + gi];
-        }
-        if (MIXED) v32[k][c] = (float)A.v[c * N + gi];
-      }
-      if (LSM) {
-        const int nn = A.nnb[gi];
-        const uint32_t* row = A.nb + g.nb_off + lo + li;
-        for (int j = 0; j < nn; j++) lst[j * lstride + li] = __ldg(row + (int64_t)j * n);
-      }
-    }
-  }
-  auto publish64 = [&](int k) {
-    int li = tid + k * nthr;
-    int64_t gi = base + li;
-    double o[3];
-    cell_origin<D>(H, g.nc, A.cell[gi], o);
-    double* q = pub[li].q64;
-    for (int c = 0; c < D; c++) q[c] = A.x[c * N + gi] - o[c];
-  };
-#pragma unroll
-  for (int k = 0; k < APT; k++)
-    if (tid + k * nthr < cnt) publish64(k);
-  int mode = kModeEval64;
-  cl.sync();
-
-  for (;;) {
-    // ================= force phase =================
-    double r[kNumRed];
-#pragma unroll
-    for (int m = 0; m < kNumRed; m++) r[m] = 0.0;
-    double F[APT][3];  // FP64 mode / FP64 evaluations
-    float Fu[APT][3];  // mixed: force used by the FP32 update
-#pragma unroll
-    for (int k = 0; k < APT; k++) {
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        F[k][c] = 0.0;
-        Fu[k][c] = 0.0f;
-      }
-      int li = tid + k * nthr;
-      if (li >= cnt) continue;
-      int64_t gi = base + li;
-      const uint32_t* row = A.nb + g.nb_off + lo + li;
-      const int nn = A.nnb[gi];
-      const int ti = ty[k];
-      if (mode == kModeEval64) {
-        double qi[3], e = 0.0, w = 0.0;
-        load_pub64<D>(&pub[li], qi);
-        for (int j = 0; j < nn; j++) {
-          uint32_t ent = LSM ? lst[j * lstride + li] : __ldg(row + (int64_t)j * n);
-          double qj[3], d[3];
-          load_pub64<D>(rpub[nb_owner(ent)] + nb_slot(ent), qj);
-          const double* of = off64 + 3 * nb_code(ent);
-#pragma unroll
-          for (int c = 0; c < D; c++) d[c] = (qj[c] - qi[c]) + of[c];
-          pair64<D>(coef[ti * A.nt + nb_type(ent)], d, F[k], want_e, e, w);
-        }
-        r[6] += e;
-        r[7] += w;
-        double f2 = 0.0, pv = 0.0, v2 = 0.0, u2 = 0.0;
-#pragma unroll
-        for (int c = 0; c < D; c++) {
-          double vc = MIXED ? (double)v32[k][c] : A.v[c * N + gi];
-          f2 = fma(F[k][c], F[k][c], f2);
-          pv = fma(F[k][c], vc, pv);
-          v2 = fma(vc, vc, v2);
-          double u = A.x[c * N + gi] - A.xb[c * N + gi];
-          u2 = fma(u, u, u2);
-        }
-        if (MIXED) {
-#pragma unroll
-          for (int c = 0; c < D; c++) {
-            fr32[k][c] = (float)F[k][c];
-            Fu[k][c] = fr32[k][c];
-            q32[k][c] = (float)qi[c];
-          }
-        }
-        r[0] = nmax(r[0], f2);
-        r[1] += pv;
-        r[2] += f2;
-        r[3] += v2;
-        r[5] = nmax(r[5], u2);
-      } else {
-        float qi[3], di[3], f[3] = {0.f, 0.f, 0.f};
-        load_pub32<D>(&pub[li], qi, di);
-        for (int j = 0; j < nn; j++) {
-          uint32_t ent = LSM ? lst[j * lstride + li] : __ldg(row + (int64_t)j * n);
-          float qj[3], dj[3], d0[3], e[3];
-          load_pub32<D>(rpub[nb_owner(ent)] + nb_slot(ent), qj, dj);
-          const float* of = off32 + 3 * nb_code(ent);
-#pragma unroll
-          for (int c = 0; c < D; c++) {
-            d0[c] = (qj[c] - qi[c]) + of[c];
-            e[c] = dj[c] - di[c];
-          }
-          pair_dev<D>(coef[ti * A.nt + nb_type(ent)], d0, e, f);
-        }
-        float f2 = 0.f, pv = 0.f, v2 = 0.f, dd = 0.f;
-#pragma unroll
-        for (int c = 0; c < D; c++) {
-          Fu[k][c] = fr32[k][c] + f[c];
-          f2 = fmaf(Fu[k][c], Fu[k][c], f2);
-          pv = fmaf(Fu[k][c], v32[k][c], pv);
-          v2 = fmaf(v32[k][c], v32[k][c], v2);
-          dd = fmaf(d32[k][c], d32[k][c], dd);
-        }
-        r[0] = nmax(r[0], (double)f2);
-        r[1] += (double)pv;
-        r[2] += (double)f2;
-        r[3] += (double)v2;
-        r[4] = nmax(r[4], (double)dd);
-      }
-    }
-
-    // ================= reduction (FP64, fixed order) =================
-#pragma unroll
-    for (int m = 0; m < kNumRed; m++) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        double t = __shfl_xor_sync(0xffffffffu, r[m], o);
-        r[m] = is_max_slot(m) ? nmax(r[m], t) : r[m] + t;
-      }
-    }
-    if (lane == 0)
-      for (int m = 0; m < kNumRed; m++) wred[warp * kNumRed + m] = r[m];
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-      for (int m = 0; m < kNumRed; m++) {
-        double t = lane < nwarp ? wred[lane * kNumRed + m] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          double u = __shfl_xor_sync(0xffffffffu, t, o);
-          t = is_max_slot(m) ? nmax(t, u) : t + u;
-        }
-        if (lane == 0) red[m] = t;
-      }
-    }
-    cl.sync();  // (A) partials of every CTA visible; all force phases done
-    if (warp == 0) {
-      double T[kNumRed];
-#pragma unroll
-      for (int m = 0; m < kNumRed; m++) {
-        double t = lane < C ? rred[lane][m] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          double u = __shfl_xor_sync(0xffffffffu, t, o);
-          t = is_max_slot(m) ? nmax(t, u) : t + u;
-        }
-        T[m] = t;
-      }
-      // ================= decisions (thread 0; identical in every CTA) ====
-      if (lane == 0) {
-        const bool was64 = mode == kModeEval64;
-        if (was64) evals++;
-        else evals32++;
-        fmx = sqrt(T[0]);
-        const bool finite = (T[0] < INFINITY) && (T[2] < INFINITY) && (T[1] == T[1]) &&
-                            (!was64 || !want_e || (fabs(T[6]) < INFINITY));
-        double umax;
-        if (!MIXED || was64) {
-          umax = sqrt(T[5]);
-          if (MIXED) wmax = umax;
-        } else {
-          umax = wmax + sqrt(T[4]);
-        }
-        int next = -1;  // -1: FIRE move; else no-move re-evaluation in that mode
-        bool stop = false;
-        if (2.0 * umax + gamma_term > A.skin) {
-          status = kStatusRebuild;  // forces of this pass may miss pairs: discard
-          stop = true;
-        } else if (!finite) {
-          if (MIXED && !was64) next = kModeEval64;
-          else { status = AQS_ERR_NONFINITE; stop = true; }
-        } else if (was64 && fmx < fp.tol) {
-          if (want_e) {
-            E = 0.5 * T[6];
-            W = 0.5 * T[7] / vol;
-            status = AQS_OK;
-            stop = true;
-          } else {
-            want_e = true;  // one more FP64 pass at the same positions for E and tau
-            next = kModeEval64;
-          }
-        } else if (MIXED && !was64 &&
-                   (fmx < fp.tol || sqrt(T[4]) > fmin(fp.ref_ratio * fmx, fp.ref_dmax))) {
-          next = kModeEval64;  // new FP64 reference at the current positions
-        } else if (iters >= fp.max_iter) {
-          status = AQS_ERR_NOT_CONVERGED;
-          stop = true;
-        } else if (iters - iters0 >= A.launch_budget) {
-          stop = true;  // status stays "running": the next launch resumes
-        }
-        Ctl c;
-        c.stop = stop;
-        c.move = !stop && next < 0;
-        c.reset = 0;
-        c.dt = dt;
-        c.ratio = 0.0;
-        c.keep = 1.0;
-        if (c.move) {
-          const double P = T[1], F2 = T[2], V2 = T[3];
-          if (P >= 0.0) {
-            npos++;
-            if (npos > fp.n_min) {
-              dt = fmin(dt * fp.f_inc, fp.dt_max);
-              alpha *= fp.f_alpha;
-            }
-          } else {
-            npos = 0;
-            dt = fmax(dt * fp.f_dec, fp.dt_min);
-            alpha = fp.alpha0;
-            c.reset = 1;
-          }
-          // |v + dt F| after the Euler step, from the reductions already made
-          const double vn2 = c.reset ? dt * dt * F2 : V2 + 2.0 * dt * P + dt * dt * F2;
-          c.dt = dt;
-          c.ratio = alpha * sqrt(vn2 / F2);
-          c.keep = 1.0 - alpha;
-          iters++;
-          mode = (MIXED && !(was64 && fmx > kBigForce)) ? kModeDev : kModeEval64;
-        } else if (!stop) {
-          mode = kModeEval64;
-        }
-        c.mode = mode;
-        c.want_e = want_e;
-        c.was64 = was64;
-        ctl = c;
-      }
-    }
-    __syncthreads();
-    const Ctl c = ctl;
-    mode = c.mode;
-    want_e = c.want_e;
-    if (c.stop) break;
-
-    if (c.move) {
-      // ================= FIRE update =================
-      if (MIXED && c.was64) {
-        // step after an FP64 evaluation: FP64 arithmetic (forces may be huge)
-#pragma unroll
-        for (int k = 0; k < APT; k++) {
-          int li = tid + k * nthr;
-          if (li >= cnt) continue;
-          double sv[3], mx = 0.0;
-#pragma unroll
-          for (int cc = 0; cc < D; cc++) {
-            double vc = c.reset ? 0.0 : (double)v32[k][cc];
-            vc = fma(c.keep, fma(c.dt, F[k][cc], vc), c.ratio * F[k][cc]);
-            v32[k][cc] = (float)vc;
-            sv[cc] = c.dt * vc;
-            mx = fmax(mx, fabs(sv[cc]));
-          }
-          double scale = 1.0;
-          if (mx > 0.5 * fp.max_step) {
-            double l2 = 0.0;
-#pragma unroll
-            for (int cc = 0; cc < D; cc++) l2 += (sv[cc] / mx) * (sv[cc] / mx);
-            double len = mx * sqrt(l2);
-            if (len > fp.max_step) scale = fp.max_step / len;
-          }
-#pragma unroll
-          for (int cc = 0; cc < D; cc++) d32[k][cc] = (float)((double)d32[k][cc] + scale * sv[cc]);
-          if (c.mode == kModeDev) {
-            store_pub32<D>(&pub[li], q32[k], d32[k]);
-          } else {  // the next evaluation is FP64: fold delta into x and publish it
-            int64_t gi = base + li;
-            for (int cc = 0; cc < D; cc++) {
-              A.x[cc * N + gi] += (double)d32[k][cc];
-              d32[k][cc] = 0.0f;
-            }
-            publish64(k);
-          }
-        }
-      } else if (MIXED) {
-        const float dtf = (float)c.dt, kf = (float)c.keep, rf = (float)c.ratio;
-        const float ms = (float)fp.max_step;
-#pragma unroll
-        for (int k = 0; k < APT; k++) {
-          int li = tid + k * nthr;
-          if (li >= cnt) continue;
-          float sv[3], mx = 0.0f;
-#pragma unroll
-          for (int cc = 0; cc < D; cc++) {
-            float vc = c.reset ? 0.0f : v32[k][cc];
-            vc = fmaf(kf, fmaf(dtf, Fu[k][cc], vc), rf * Fu[k][cc]);
-            v32[k][cc] = vc;
-            sv[cc] = dtf * vc;
-            mx = fmaxf(mx, fabsf(sv[cc]));
-          }
-          float scale = 1.0f;
-          if (mx > 0.5f * ms) {
-            float l2 = 0.0f;
-#pragma unroll
-            for (int cc = 0; cc < D; cc++) l2 = fmaf(sv[cc] / mx, sv[cc] / mx, l2);
-            float len = mx * sqrtf(l2);
-            if (len > ms) scale = ms / len;
-          }
-#pragma unroll
-          for (int cc = 0; cc < D; cc++) d32[k][cc] = fmaf(scale, sv[cc], d32[k][cc]);
-          if (c.mode == kModeDev) {
-            store_pub32<D>(&pub[li], q32[k], d32[k]);
-          } else {  // the next evaluation is FP64: fold delta into x and publish it
-            int64_t gi = base + li;
-            for (int cc = 0; cc < D; cc++) {
-              A.x[cc * N + gi] += (double)d32[k][cc];
-              d32[k][cc] = 0.0f;
-            }
-            publish64(k);
-          }
-        }
-      } else {
-        const double cdt = c.dt, keep = c.keep, ratio = c.ratio;
-#pragma unroll
-        for (int k = 0; k < APT; k++) {
-          int li = tid + k * nthr;
-          if (li >= cnt) continue;
-          int64_t gi = base + li;
-          double s[3], mx = 0.0;
-#pragma unroll
-          for (int cc = 0; cc < D; cc++) {
-            double vc = c.reset ? 0.0 : A.v[cc * N + gi];
-            vc = fma(keep, fma(cdt, F[k][cc], vc), ratio * F[k][cc]);
-            A.v[cc * N + gi] = vc;
-            s[cc] = cdt * vc;
-            mx = fmax(mx, fabs(s[cc]));
-          }
-          double scale = 1.0;
-          if (mx > 0.5 * fp.max_step) {
-            double l2 = 0.0;
-#pragma unroll
-            for (int cc = 0; cc < D; cc++) l2 += (s[cc] / mx) * (s[cc] / mx);
-            double len = mx * sqrt(l2);
-            if (len > fp.max_step) scale = fp.max_step / len;
-          }
-#pragma unroll
-          for (int cc = 0; cc < D; cc++) A.x[cc * N + gi] = fma(scale, s[cc], A.x[cc * N + gi]);
-          publish64(k);
-        }
-      }
-    } else if (MIXED && c.mode == kModeEval64) {
-      // no move: fold delta into the reference and publish FP64 positions
-#pragma unroll
-      for (int k = 0; k < APT; k++) {
-        int li = tid + k * nthr;
-        if (li >= cnt) continue;
-        int64_t gi = base + li;
-        for (int cc = 0; cc < D; cc++) {
-          A.x[cc * N + gi] += (double)d32[k][cc];
-          d32[k][cc] = 0.0f;
-        }
-        publish64(k);
-      }
-    }
-    cl.sync();  // (B) new positions visible; partial slots free again
-  }
-
-  // ---- exit: materialise x = x_ref + delta, keep v, store the FIRE state ----
-  if (MIXED) {
-#pragma unroll
-    for (int k = 0; k < APT; k++) {
-      int li = tid + k * nthr;
-      if (li >= cnt) continue;
-      int64_t gi = base + li;
-      for (int cc = 0; cc < D; cc++) {
-        A.x[cc * N + gi] += (double)d32[k][cc];
-        A.v[cc * N + gi] = (double)v32[k][cc];
-      }
-    }
-  }
-  if (rank == 0 && tid == 0) {
-    st->dt = dt;
-    st->alpha = alpha;
-    st->npos = npos;
-    st->iters = iters;
-    st->evals64 = evals;
-    st->evals32 = evals32;
-    st->status = status;
-    st->fmax = fmx;
-    st->fresh = 0;
-    if (status == AQS_OK) {
-      st->E = E;
-      st->tau = W;
-    }
-  }
-  cl.sync();  // nobody leaves while others may still read its shared memory
-}
-
-// ---------------------------------------------------------------- launcher
-static size_t smem_fixed(int dim, int nt) {
-  (void)dim;
-  return sizeof(double) * (kNumRed * 33 + 27 * 3) + sizeof(float) * (27 * 3 + 3) +
-         sizeof(PairCoef) * nt * nt + 64;
-}
-
-size_t minimize_smem_bytes(int dim, int npc, int nt, int cap, bool list_in_smem) {
-  size_t pub = (dim == 2 ? sizeof(Pub<2>) : sizeof(Pub<3>)) * (size_t)npc;
-  return pub + smem_fixed(dim, nt) + (list_in_smem ? sizeof(uint32_t) * (size_t)cap * npc : 0);
-}
-
-template <int D, bool MIXED, int APT, bool LSM>
-static cudaError_t launch_t(const MinArgs& a, int n_clusters, int C, int threads, size_t smem,
-                            cudaStream_t s) {
-  auto kern = k_minimize<D, MIXED, APT, LSM>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (C > 8) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = C;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(n_clusters * C);
-  cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  count_launch();
-  return cudaLaunchKernelEx(&cfg, kern, a);
-}
-
-template <int D, bool MIXED, bool LSM>
-static cudaError_t launch_apt(const MinArgs& a, int n_clusters, int C, int npc, size_t smem,
-                              cudaStream_t s) {
-  int apt = npc <= 512 ? 1 : (npc <= 1024 ? 2 : (npc <= 2048 ? 4 : 8));
-  int threads = (npc + apt - 1) / apt;
-  threads = ((threads + 31) / 32) * 32;
-  if (threads > 512) return cudaErrorInvalidValue;
-  switch (apt) {
-    case 1: return launch_t<D, MIXED, 1, LSM>(a, n_clusters, C, threads, smem, s);
-    case 2: return launch_t<D, MIXED, 2, LSM>(a, n_clusters, C, threads, smem, s);
-    case 4: return launch_t<D, MIXED, 4, LSM>(a, n_clusters, C, threads, smem, s);
-    default: return launch_t<D, MIXED, 8, LSM>(a, n_clusters, C, threads, smem, s);
-  }
+static cudaError_t dispatch(int dim, bool mixed, const MinArgs* a, int n_clusters, int C, int npc,
+                            int nrep, int nt, int cap, cudaStream_t s, int* max_clusters) {
+  int mem = choose_mem(dim, npc, nrep, nt, cap);
+  size_t smem = minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, mem);
+  if (dim == 2)
+    return mixed ? run_mem_2_mixed(mem, a, n_clusters, C, npc, smem, s, max_clusters)
+                 : run_mem_2_fp64(mem, a, n_clusters, C, npc, smem, s, max_clusters);
+  return mixed ? run_mem_3_mixed(mem, a, n_clusters, C, npc, smem, s, max_clusters)
+               : run_mem_3_fp64(mem, a, n_clusters, C, npc, smem, s, max_clusters);
 }
 
 cudaError_t launch_minimize(int dim, bool mixed, MinArgs a, int n_clusters, int C, int npc,
-                            int cap, cudaStream_t s) {
+                            int nrep, int cap, cudaStream_t s) {
   a.npc_launch = npc;
-  const size_t limit = 220 * 1024;
-  bool lsm = minimize_smem_bytes(dim, npc, a.nt, cap, true) <= limit;
-  size_t smem = minimize_smem_bytes(dim, npc, a.nt, cap, lsm);
-  if (dim == 2) {
-    if (mixed) return lsm ? launch_apt<2, true, true>(a, n_clusters, C, npc, smem, s)
-                          : launch_apt<2, true, false>(a, n_clusters, C, npc, smem, s);
-    return lsm ? launch_apt<2, false, true>(a, n_clusters, C, npc, smem, s)
-               : launch_apt<2, false, false>(a, n_clusters, C, npc, smem, s);
+  a.nrep_launch = nrep;
+  return dispatch(dim, mixed, &a, n_clusters, C, npc, nrep, a.nt, cap, s, nullptr);
+}
+
+int minimize_max_active_clusters(int dim, bool mixed, int C, int npc, int nrep, int nt, int cap) {
+  int m = 0;
+  if (dispatch(dim, mixed, nullptr, 1, C, npc, nrep, nt, cap, nullptr, &m) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
   }
-  if (mixed) return lsm ? launch_apt<3, true, true>(a, n_clusters, C, npc, smem, s)
-                        : launch_apt<3, true, false>(a, n_clusters, C, npc, smem, s);
-  return lsm ? launch_apt<3, false, true>(a, n_clusters, C, npc, smem, s)
-             : launch_apt<3, false, false>(a, n_clusters, C, npc, smem, s);
+  return m;
 }
 
 }  // namespace aqs

@@ -25,10 +25,13 @@ struct MinArgs {
   double skin, rlist;
   int64_t launch_budget;  // FIRE iterations per launch before yielding
   int npc_launch;         // shared-memory stride (largest npc of the launch)
+  int nrep_launch;        // largest replica of the launch (staged positions)
 };
 
-size_t minimize_smem_bytes(int dim, int npc, int nt, int cap, bool list_in_smem);
+size_t minimize_smem_bytes(int dim, int npc, int nrep, int nt, int cap, int mem);
 cudaError_t launch_minimize(int dim, bool mixed, MinArgs a, int n_clusters, int C, int npc,
-                            int cap, cudaStream_t s);
+                            int nrep, int cap, cudaStream_t s);
+// clusters of C CTAs that can be resident at once for this configuration
+int minimize_max_active_clusters(int dim, bool mixed, int C, int npc, int nrep, int nt, int cap);
 
 }  // namespace aqs

@@ -1,0 +1,94 @@
+// minimize_launch.cuh -- launch helpers of the minimiser instantiations.
+#pragma once
+#include "minimize_kernel.cuh"
+
+namespace aqs {
+
+inline size_t smem_fixed(int nt) {
+  return sizeof(double) * (kNumRed * 33 + 27 * 3) + sizeof(float) * (27 * 3 + 3) +
+         sizeof(PairCoef) * nt * nt + 64;
+}
+
+inline size_t pub_size(int dim) { return dim == 2 ? sizeof(Pub<2>) : sizeof(Pub<3>); }
+
+inline size_t minimize_smem_bytes_impl(int dim, int npc, int nrep, int nt, int cap, int mem) {
+  size_t pub = pub_size(dim) * (size_t)(mem == 2 ? nrep : npc);
+  return pub + smem_fixed(nt) + (mem >= 1 ? sizeof(uint32_t) * (size_t)cap * npc : 0);
+}
+
+constexpr size_t kSmemLimit = 220 * 1024;
+
+inline int choose_mem(int dim, int npc, int nrep, int nt, int cap) {
+  if (minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, 2) <= kSmemLimit) return 2;
+  if (minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, 1) <= kSmemLimit) return 1;
+  return 0;
+}
+
+inline void choose_apt(int npc, int* apt, int* threads) {
+  *apt = npc <= 512 ? 1 : (npc <= 1024 ? 2 : (npc <= 2048 ? 4 : 8));
+  int t = (npc + *apt - 1) / *apt;
+  *threads = ((t + 31) / 32) * 32;
+}
+
+template <int D, bool MIXED, int APT, int MEM>
+cudaError_t run_t(const MinArgs* a, int n_clusters, int C, int threads, size_t smem,
+                         cudaStream_t s, int* max_clusters) {
+  auto kern = k_minimize<D, MIXED, APT, MEM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(n_clusters * C);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (max_clusters) return cudaOccupancyMaxActiveClusters(max_clusters, kern, &cfg);
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, kern, *a);
+}
+
+template <int D, bool MIXED, int MEM>
+cudaError_t run_apt(const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
+                           cudaStream_t s, int* max_clusters) {
+  int apt, threads;
+  choose_apt(npc, &apt, &threads);
+  if (threads > 512) return cudaErrorInvalidValue;
+  switch (apt) {
+    case 1: return run_t<D, MIXED, 1, MEM>(a, n_clusters, C, threads, smem, s, max_clusters);
+    case 2: return run_t<D, MIXED, 2, MEM>(a, n_clusters, C, threads, smem, s, max_clusters);
+    case 4: return run_t<D, MIXED, 4, MEM>(a, n_clusters, C, threads, smem, s, max_clusters);
+    default: return run_t<D, MIXED, 8, MEM>(a, n_clusters, C, threads, smem, s, max_clusters);
+  }
+}
+
+template <int D, bool MIXED>
+cudaError_t run_mem(int mem, const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
+                           cudaStream_t s, int* max_clusters) {
+  switch (mem) {
+    case 2: return run_apt<D, MIXED, 2>(a, n_clusters, C, npc, smem, s, max_clusters);
+    case 1: return run_apt<D, MIXED, 1>(a, n_clusters, C, npc, smem, s, max_clusters);
+    default: return run_apt<D, MIXED, 0>(a, n_clusters, C, npc, smem, s, max_clusters);
+  }
+}
+
+// one instantiation unit per (dimension, precision)
+cudaError_t run_mem_2_fp64(int mem, const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
+                           cudaStream_t s, int* max_clusters);
+cudaError_t run_mem_2_mixed(int mem, const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
+                            cudaStream_t s, int* max_clusters);
+cudaError_t run_mem_3_fp64(int mem, const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
+                           cudaStream_t s, int* max_clusters);
+cudaError_t run_mem_3_mixed(int mem, const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
+                            cudaStream_t s, int* max_clusters);
+
+}  // namespace aqs

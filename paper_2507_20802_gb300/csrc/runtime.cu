@@ -160,12 +160,27 @@ void cell_widths(int D, const double* H, double* w) {
   if (D == 3) w[2] = H[8];
 }
 
-int auto_cluster(int R, int64_t n) {
-  int C = std::max(1, 152 / std::max(1, R));
-  C = std::min(C, kMaxCluster);
-  C = (int)std::min<int64_t>(C, std::max<int64_t>(1, n / 32));
-  while ((n + C - 1) / C > 4096 && C < kMaxCluster) C++;
-  return C;
+// Cluster size for R replicas of n atoms: the largest C for which all R
+// clusters are resident at once (so every chain advances in every wave);
+// otherwise the C with the most resident CTAs.  At least 32 atoms per CTA and
+// at most 4096.
+int auto_cluster(int dim, bool mixed, int R, int64_t n, int nt, int cap) {
+  int best = 1;
+  double best_score = -1.0;
+  for (int C = kMaxCluster; C >= 1; C--) {
+    int64_t npc = (n + C - 1) / C;
+    if (npc > 4096) break;
+    if (C > 1 && n / C < 32) continue;
+    int m = minimize_max_active_clusters(dim, mixed, C, (int)npc, (int)n, nt, cap);
+    if (m <= 0) continue;
+    if (m >= R) return C;
+    double score = (double)std::min(R, m) * C;
+    if (score > best_score) {
+      best_score = score;
+      best = C;
+    }
+  }
+  return best;
 }
 
 aqs_status upload_geom(aqs_system* s) {
@@ -382,6 +397,7 @@ MinArgs min_args(aqs_system* s, const aqs_fire_params* f) {
   a.rlist = s->rlist;
   a.launch_budget = 4096;
   a.npc_launch = 0;
+  a.nrep_launch = 0;
   return a;
 }
 
@@ -449,11 +465,13 @@ aqs_status minimize_impl(aqs_system* s, const aqs_fire_params* f, const std::vec
     if (timing) CUDA_TRY(cudaEventRecord(s->ev0, s->stream));
     for (size_t gi = 0; gi < groups.size(); gi++) {
       int C = Cs[gi];
-      int npc = 0;
-      for (int k = 0; k < groups[gi].second; k++)
+      int npc = 0, nrep = 0;
+      for (int k = 0; k < groups[gi].second; k++) {
         npc = std::max(npc, s->geom[order_work[groups[gi].first + k]].npc);
+        nrep = std::max(nrep, s->geom[order_work[groups[gi].first + k]].n);
+      }
       a.work = s->d_work + groups[gi].first;
-      CUDA_TRY(launch_minimize(s->dim, s->prec == AQS_MIXED, a, groups[gi].second, C, npc,
+      CUDA_TRY(launch_minimize(s->dim, s->prec == AQS_MIXED, a, groups[gi].second, C, npc, nrep,
                                s->cap, s->stream));
     }
     if (timing) CUDA_TRY(cudaEventRecord(s->ev1, s->stream));
@@ -608,7 +626,8 @@ aqs_status init_system(aqs_system* s, int dim, int R, const int64_t* n, const aq
     RepGeom& g = s->geom[r];
     g.off = s->off[r];
     g.n = (int)n[r];
-    int C = C_override > 0 ? C_override : auto_cluster(R, n[r]);
+    int C = C_override > 0 ? C_override
+                           : auto_cluster(dim, prec == AQS_MIXED, R, n[r], s->nt, s->cap);
     C = std::max(1, std::min(C, kMaxCluster));
     g.C = C;
     g.npc = (int)((n[r] + C - 1) / C);
