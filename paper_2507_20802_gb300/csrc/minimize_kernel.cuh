@@ -153,9 +153,32 @@ constexpr int kModeEval64 = 0, kModeDev = 1;
 // Control block written once per iteration by thread 0 of every CTA (all CTAs
 // compute it from bitwise identical totals) and read by the CTA's threads.
 struct Ctl {
-  double dt, ratio, keep;
+  double dt, ratio, keep;     // FIRE step after an FP64 evaluation
+  float dtf, ratiof, keepf;   // the same in FP32 for the FP32 update
   int move, mode, stop, reset, want_e, was64;
 };
+
+// Compensated ("float-float") sum on the FP32 pipe: TwoSum of Knuth (TAOCP
+// vol. 2, 4.2.2) followed by renormalisation (Dekker 1971).  The pair
+// (hi, lo) carries about 44 significant bits, so cross-thread sums of the FIRE
+// reductions keep FP64-level accuracy without FP64 instructions, whose issue
+// cost on GB300 (about 64 cycles per warp instruction per SM sub-partition)
+// would dominate an iteration.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  float s = a.hi + b.hi;
+  float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  float hi = s + e;
+  return FF{hi, e - (hi - s)};
+}
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
+  return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ float nmaxf(float a, float b) { return (a != a || a > b) ? a : b; }
 
 // While the largest FP64 force exceeds this, mixed mode keeps evaluating in
 // FP64 (random starts and collisions), where FP32 would overflow.
@@ -224,6 +247,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   // FIRE scalars: meaningful in thread 0 only
   double dt = fresh ? fp.dt0 : st->dt;
   double alpha = fresh ? fp.alpha0 : st->alpha;
+  float dtf = (float)dt, alphaf = (float)alpha;  // mixed mode keeps these in FP32
   int npos = fresh ? 0 : st->npos;
   int64_t iters = fresh ? 0 : st->iters;
   int64_t evals = fresh ? 0 : st->evals64;
@@ -232,7 +256,11 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   const double gamma_term = fabs(H[0 * D + 1] - g.tilt_b) / H[1 * D + 1] * A.rlist;
   const double vol = D == 2 ? H[0] * H[3] : H[0] * H[4] * H[8];
   bool want_e = MIXED;  // mixed: every FP64 evaluation also gives E and tau
-  double wmax = 0.0;    // max |x_ref - x_b| at the last FP64 evaluation (mixed)
+  float wmaxf = 0.0f;   // max |x_ref - x_b| at the last FP64 evaluation (mixed)
+  const float gamma_termf = (float)gamma_term, skinf = (float)A.skin;
+  const float tolf = (float)fp.tol, ratio_f = (float)fp.ref_ratio, dmax_f = (float)fp.ref_dmax;
+  const float f_incf = (float)fp.f_inc, f_decf = (float)fp.f_dec, f_alphaf = (float)fp.f_alpha;
+  const float dt_maxf = (float)fp.dt_max, dt_minf = (float)fp.dt_min, alpha0f = (float)fp.alpha0;
   int status = kStatusRunning;
   double E = 0.0, W = 0.0, fmx = 0.0;
 
@@ -301,6 +329,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
     double r[kNumRed];
 #pragma unroll
     for (int m = 0; m < kNumRed; m++) r[m] = 0.0;
+    float rf[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // DEV: fmax^2, P, |F|^2, |v|^2, max|delta|^2
     double F[APT][3];  // FP64 mode / FP64 evaluations
     float Fu[APT][3];  // mixed: force used by the FP32 update
 #pragma unroll
@@ -381,75 +410,201 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
           v2 = fmaf(v32[k][c], v32[k][c], v2);
           dd = fmaf(d32[k][c], d32[k][c], dd);
         }
-        r[0] = nmax(r[0], (double)f2);
-        r[1] += (double)pv;
-        r[2] += (double)f2;
-        r[3] += (double)v2;
-        r[4] = nmax(r[4], (double)dd);
+        rf[0] = nmaxf(rf[0], f2);
+        rf[1] += pv;
+        rf[2] += f2;
+        rf[3] += v2;
+        rf[4] = nmaxf(rf[4], dd);
       }
     }
 
-    // ================= reduction (FP64, fixed order) =================
+    // ================= reduction (fixed order; FP64 or float-float) =================
+    const bool fast = MIXED && mode == kModeDev;  // uniform in the cluster
+    double T[kNumRed];  // FP64 totals (valid in warp 0)
+    float Tf[5];        // DEV totals (valid in warp 0)
+    if (!fast) {
 #pragma unroll
-    for (int m = 0; m < kNumRed; m++) {
+      for (int m = 0; m < kNumRed; m++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          double t = __shfl_xor_sync(0xffffffffu, r[m], o);
+          r[m] = is_max_slot(m) ? nmax(r[m], t) : r[m] + t;
+        }
+      }
+      if (lane == 0)
+        for (int m = 0; m < kNumRed; m++) wred[warp * kNumRed + m] = r[m];
+      __syncthreads();
+      if (warp == 0) {
+#pragma unroll
+        for (int m = 0; m < kNumRed; m++) {
+          double t = lane < nwarp ? wred[lane * kNumRed + m] : 0.0;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            double u = __shfl_xor_sync(0xffffffffu, t, o);
+            t = is_max_slot(m) ? nmax(t, u) : t + u;
+          }
+          if (lane == 0) red[m] = t;
+        }
+      }
+      cl.sync();  // (A) partials of every CTA visible; all force phases done
+      if (warp == 0) {
+#pragma unroll
+        for (int m = 0; m < kNumRed; m++) {
+          double t = lane < C ? rred[lane][m] : 0.0;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            double u = __shfl_xor_sync(0xffffffffu, t, o);
+            t = is_max_slot(m) ? nmax(t, u) : t + u;
+          }
+          T[m] = t;
+        }
+      }
+    } else {
+      float m0 = rf[0], m4 = rf[4];
+      FF sp{rf[1], 0.f}, sf{rf[2], 0.f}, sv{rf[3], 0.f};
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        double t = __shfl_xor_sync(0xffffffffu, r[m], o);
-        r[m] = is_max_slot(m) ? nmax(r[m], t) : r[m] + t;
+        m0 = nmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m4 = nmaxf(m4, __shfl_xor_sync(0xffffffffu, m4, o));
+        sp = ff_add(sp, ff_shfl_xor(sp, o));
+        sf = ff_add(sf, ff_shfl_xor(sf, o));
+        sv = ff_add(sv, ff_shfl_xor(sv, o));
       }
-    }
-    if (lane == 0)
-      for (int m = 0; m < kNumRed; m++) wred[warp * kNumRed + m] = r[m];
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-      for (int m = 0; m < kNumRed; m++) {
-        double t = lane < nwarp ? wred[lane * kNumRed + m] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          double u = __shfl_xor_sync(0xffffffffu, t, o);
-          t = is_max_slot(m) ? nmax(t, u) : t + u;
-        }
-        if (lane == 0) red[m] = t;
-      }
-    }
-    cl.sync();  // (A) partials of every CTA visible; all force phases done
-    if (warp == 0) {
-      double T[kNumRed];
-#pragma unroll
-      for (int m = 0; m < kNumRed; m++) {
-        double t = lane < C ? rred[lane][m] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          double u = __shfl_xor_sync(0xffffffffu, t, o);
-          t = is_max_slot(m) ? nmax(t, u) : t + u;
-        }
-        T[m] = t;
-      }
-      // ================= decisions (thread 0; identical in every CTA) ====
+      float* w32 = reinterpret_cast<float*>(wred);
       if (lane == 0) {
-        const bool was64 = mode == kModeEval64;
-        if (was64) evals++;
-        else evals32++;
-        fmx = sqrt(T[0]);
-        const bool finite = (T[0] < INFINITY) && (T[2] < INFINITY) && (T[1] == T[1]) &&
-                            (!was64 || !want_e || (fabs(T[6]) < INFINITY));
-        double umax;
-        if (!MIXED || was64) {
-          umax = sqrt(T[5]);
-          if (MIXED) wmax = umax;
-        } else {
-          umax = wmax + sqrt(T[4]);
+        float* q = w32 + warp * 8;
+        q[0] = m0; q[1] = m4; q[2] = sp.hi; q[3] = sp.lo;
+        q[4] = sf.hi; q[5] = sf.lo; q[6] = sv.hi; q[7] = sv.lo;
+      }
+      __syncthreads();
+      // butterfly over 8-float records (max, max, three float-float sums)
+      auto reduce8 = [&](const float* q, bool valid, float* out) {
+        float a0 = valid ? q[0] : 0.f, a4 = valid ? q[1] : 0.f;
+        FF bp{valid ? q[2] : 0.f, valid ? q[3] : 0.f}, bf{valid ? q[4] : 0.f, valid ? q[5] : 0.f};
+        FF bv{valid ? q[6] : 0.f, valid ? q[7] : 0.f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a0 = nmaxf(a0, __shfl_xor_sync(0xffffffffu, a0, o));
+          a4 = nmaxf(a4, __shfl_xor_sync(0xffffffffu, a4, o));
+          bp = ff_add(bp, ff_shfl_xor(bp, o));
+          bf = ff_add(bf, ff_shfl_xor(bf, o));
+          bv = ff_add(bv, ff_shfl_xor(bv, o));
         }
-        int next = -1;  // -1: FIRE move; else no-move re-evaluation in that mode
-        bool stop = false;
-        if (2.0 * umax + gamma_term > A.skin) {
+        out[0] = a0; out[1] = a4; out[2] = bp.hi; out[3] = bp.lo;
+        out[4] = bf.hi; out[5] = bf.lo; out[6] = bv.hi; out[7] = bv.lo;
+      };
+      float* red32 = reinterpret_cast<float*>(red);
+      if (warp == 0) {
+        float o8[8];
+        reduce8(w32 + lane * 8, lane < nwarp, o8);
+        if (lane == 0)
+          for (int m = 0; m < 8; m++) red32[m] = o8[m];
+      }
+      cl.sync();  // (A) partials of every CTA visible; all force phases done
+      if (warp == 0) {
+        float o8[8];
+        const float* rq = lane < C ? reinterpret_cast<const float*>(rred[lane]) : red32;
+        reduce8(rq, lane < C, o8);
+        Tf[0] = o8[0];
+        Tf[4] = o8[1];
+        Tf[1] = o8[2] + o8[3];
+        Tf[2] = o8[4] + o8[5];
+        Tf[3] = o8[6] + o8[7];
+      }
+    }
+
+    // ================= decisions (thread 0; identical in every CTA) =================
+    if (warp == 0 && lane == 0) {
+      const bool was64 = mode == kModeEval64;
+      int next = -1;  // -1: FIRE move; else no-move re-evaluation in that mode
+      bool stop = false;
+      Ctl c;
+      c.reset = 0;
+      if (MIXED) {
+        float fm, umax, P, F2, V2;
+        bool finite;
+        if (was64) {
+          evals++;
+          fmx = sqrt(T[0]);
+          fm = (float)fmx;
+          finite = (T[0] < INFINITY) && (T[2] < INFINITY) && (T[1] == T[1]) &&
+                   (!want_e || fabs(T[6]) < INFINITY);
+          umax = sqrtf((float)T[5]);
+          wmaxf = umax;
+          P = (float)T[1];
+          F2 = (float)T[2];
+          V2 = (float)T[3];
+        } else {
+          evals32++;
+          fm = sqrtf(Tf[0]);
+          finite = (Tf[0] < INFINITY) && (Tf[2] < INFINITY) && (Tf[1] == Tf[1]);
+          umax = wmaxf + sqrtf(Tf[4]);
+          P = Tf[1];
+          F2 = Tf[2];
+          V2 = Tf[3];
+        }
+        if (2.0f * umax + gamma_termf > skinf) {
           status = kStatusRebuild;  // forces of this pass may miss pairs: discard
           stop = true;
         } else if (!finite) {
-          if (MIXED && !was64) next = kModeEval64;
+          if (!was64) next = kModeEval64;
           else { status = AQS_ERR_NONFINITE; stop = true; }
-        } else if (was64 && fmx < fp.tol) {
+        } else if (was64 && fmx < fp.tol) {  // the convergence test, FP64
+          E = 0.5 * T[6];
+          W = 0.5 * T[7] / vol;
+          status = AQS_OK;
+          stop = true;
+        } else if (!was64 && (fm < tolf || sqrtf(Tf[4]) > fminf(ratio_f * fm, dmax_f))) {
+          next = kModeEval64;  // new FP64 reference at the current positions
+        } else if (iters >= fp.max_iter) {
+          status = AQS_ERR_NOT_CONVERGED;
+          stop = true;
+        } else if (iters - iters0 >= A.launch_budget) {
+          stop = true;  // status stays "running": the next launch resumes
+        }
+        c.stop = stop;
+        c.move = !stop && next < 0;
+        c.dtf = dtf;
+        c.ratiof = 0.f;
+        c.keepf = 1.f;
+        if (c.move) {
+          if (P >= 0.0f) {
+            npos++;
+            if (npos > fp.n_min) {
+              dtf = fminf(dtf * f_incf, dt_maxf);
+              alphaf *= f_alphaf;
+            }
+          } else {
+            npos = 0;
+            dtf = fmaxf(dtf * f_decf, dt_minf);
+            alphaf = alpha0f;
+            c.reset = 1;
+          }
+          const float vn2 = c.reset ? dtf * dtf * F2 : V2 + 2.0f * dtf * P + dtf * dtf * F2;
+          c.dtf = dtf;
+          c.ratiof = alphaf * sqrtf(vn2 / F2);
+          c.keepf = 1.0f - alphaf;
+          iters++;
+          mode = (was64 && fmx > kBigForce) ? kModeEval64 : kModeDev;
+        } else if (!stop) {
+          mode = kModeEval64;
+        }
+        c.dt = (double)c.dtf;
+        c.ratio = (double)c.ratiof;
+        c.keep = (double)c.keepf;
+      } else {
+        evals++;
+        fmx = sqrt(T[0]);
+        const bool finite = (T[0] < INFINITY) && (T[2] < INFINITY) && (T[1] == T[1]) &&
+                            (!want_e || (fabs(T[6]) < INFINITY));
+        const double umax = sqrt(T[5]);
+        if (2.0 * umax + gamma_term > A.skin) {
+          status = kStatusRebuild;
+          stop = true;
+        } else if (!finite) {
+          status = AQS_ERR_NONFINITE;
+          stop = true;
+        } else if (fmx < fp.tol) {
           if (want_e) {
             E = 0.5 * T[6];
             W = 0.5 * T[7] / vol;
@@ -459,19 +614,14 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
             want_e = true;  // one more FP64 pass at the same positions for E and tau
             next = kModeEval64;
           }
-        } else if (MIXED && !was64 &&
-                   (fmx < fp.tol || sqrt(T[4]) > fmin(fp.ref_ratio * fmx, fp.ref_dmax))) {
-          next = kModeEval64;  // new FP64 reference at the current positions
         } else if (iters >= fp.max_iter) {
           status = AQS_ERR_NOT_CONVERGED;
           stop = true;
         } else if (iters - iters0 >= A.launch_budget) {
-          stop = true;  // status stays "running": the next launch resumes
+          stop = true;
         }
-        Ctl c;
         c.stop = stop;
         c.move = !stop && next < 0;
-        c.reset = 0;
         c.dt = dt;
         c.ratio = 0.0;
         c.keep = 1.0;
@@ -495,15 +645,15 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
           c.ratio = alpha * sqrt(vn2 / F2);
           c.keep = 1.0 - alpha;
           iters++;
-          mode = (MIXED && !(was64 && fmx > kBigForce)) ? kModeDev : kModeEval64;
-        } else if (!stop) {
-          mode = kModeEval64;
         }
-        c.mode = mode;
-        c.want_e = want_e;
-        c.was64 = was64;
-        ctl = c;
+        mode = kModeEval64;
+        c.dtf = c.ratiof = 0.f;
+        c.keepf = 1.f;
       }
+      c.mode = mode;
+      c.want_e = want_e;
+      c.was64 = was64;
+      ctl = c;
     }
     __syncthreads();
     const Ctl c = ctl;
@@ -550,7 +700,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
           }
         }
       } else if (MIXED) {
-        const float dtf = (float)c.dt, kf = (float)c.keep, rf = (float)c.ratio;
+        const float dtf = c.dtf, kf = c.keepf, rf = c.ratiof;
         const float ms = (float)fp.max_step;
 #pragma unroll
         for (int k = 0; k < APT; k++) {
@@ -646,8 +796,8 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
     }
   }
   if (rank == 0 && tid == 0) {
-    st->dt = dt;
-    st->alpha = alpha;
+    st->dt = MIXED ? (double)dtf : dt;
+    st->alpha = MIXED ? (double)alphaf : alpha;
     st->npos = npos;
     st->iters = iters;
     st->evals64 = evals;
