@@ -567,8 +567,11 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         c.dtf = dtf;
         c.ratiof = 0.f;
         c.keepf = 1.f;
+        c.dt = (double)dtf;
+        c.ratio = 0.0;
+        c.keep = 1.0;
         if (c.move) {
-          if (P >= 0.0f) {
+          if (was64 ? (T[1] >= 0.0) : (P >= 0.0f)) {
             npos++;
             if (npos > fp.n_min) {
               dtf = fminf(dtf * f_incf, dt_maxf);
@@ -580,18 +583,24 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
             alphaf = alpha0f;
             c.reset = 1;
           }
-          const float vn2 = c.reset ? dtf * dtf * F2 : V2 + 2.0f * dtf * P + dtf * dtf * F2;
-          c.dtf = dtf;
-          c.ratiof = alphaf * sqrtf(vn2 / F2);
-          c.keepf = 1.0f - alphaf;
+          if (was64) {
+            // after an FP64 evaluation the sums may exceed the FP32 range
+            const double d = dtf, a = alphaf;
+            const double vn2 = c.reset ? d * d * T[2] : T[3] + 2.0 * d * T[1] + d * d * T[2];
+            c.dt = d;
+            c.ratio = a * sqrt(vn2 / T[2]);
+            c.keep = 1.0 - a;
+          } else {
+            const float vn2 = c.reset ? dtf * dtf * F2 : V2 + 2.0f * dtf * P + dtf * dtf * F2;
+            c.dtf = dtf;
+            c.ratiof = alphaf * sqrtf(vn2 / F2);
+            c.keepf = 1.0f - alphaf;
+          }
           iters++;
           mode = (was64 && fmx > kBigForce) ? kModeEval64 : kModeDev;
         } else if (!stop) {
           mode = kModeEval64;
         }
-        c.dt = (double)c.dtf;
-        c.ratio = (double)c.ratiof;
-        c.keep = (double)c.keepf;
       } else {
         evals++;
         fmx = sqrt(T[0]);
