@@ -207,7 +207,9 @@ def main():
     def one_pass():
         nonlocal done
         remaining = n_total - done if n_total > done else P_CHAINS * K_FINE
+        torch.cuda.nvtx.range_push("aqs_pass")  # lets a profiler select the passes
         r = s.parallel_step(DGAMMA, K_FINE, P_CHAINS, remaining, fire=fire, max_iterations=1)
+        torch.cuda.nvtx.range_pop()
         done += r["accepted"]
         return r
 
