@@ -223,6 +223,38 @@ aqs_status aqs_set_box(aqs_system* sys, int replica, const double* H);
 aqs_status aqs_energy_forces(aqs_system* sys, int replica, double* energy, double* forces,
                              double* tau);
 
+/* ---- allocation-free evaluation ----
+ * The paper has no counterpart: this entry point exists for callers that
+ * must not allocate device memory (inside another library's fixed memory
+ * plan, under an allocation quota, or while holding a lock that cudaMalloc
+ * could wait on).  It computes the FP64 shifted-force LJ energy, forces and
+ * shear stress of ONE configuration by visiting all pairs (minimum image),
+ * with no system, no Verlet list and no cudaMalloc/cudaFree or other
+ * allocating call.  Its only scratch is a fixed device array inside the
+ * library (one partial sum pair per 128 atoms, AQS_NOALLOC_MAX_ATOMS atoms at
+ * most, 8 KiB held on every GPU that loads the library until the process
+ * exits).
+ *   dim       2 or 3
+ *   n         atoms, 2 <= n <= AQS_NOALLOC_MAX_ATOMS, else AQS_ERR_INVALID_ARG
+ *   pos       device [n * dim], Cartesian
+ *   types     device [n], values < pot->n_types
+ *   box       host [dim * dim], upper-triangular cell (tilt in H[0][1] only);
+ *             AQS_ERR_BOX_TOO_SMALL if 2 * max cutoff >= a perpendicular width
+ *   pot       host, the potential as in aqs_potential
+ *   forces    device [n * dim], written (force on each atom)
+ *   energy_tau device [2], written: total energy, shear stress (1/V) dU/dgamma
+ *   stream    cudaStream_t (NULL = legacy default stream); the call only
+ *             enqueues work and returns without synchronising.
+ * The first call on a device looks up the scratch array's device address with
+ * cudaGetSymbolAddress while that device is current; make that first call
+ * before capturing a stream.  Every call shares the one scratch array and each
+ * call overwrites every slot it later reads, so nothing has to be cleared, but
+ * calls that overlap on the GPU (different streams, no ordering) race on it. */
+#define AQS_NOALLOC_MAX_ATOMS 65536
+aqs_status aqs_energy_forces_noalloc(int dim, int64_t n, const double* pos, const int32_t* types,
+                                     const double* box, const aqs_potential* pot, double* forces,
+                                     double* energy_tau, void* stream);
+
 /* ---- diagnostics ---- */
 /* Counters of the persistent minimiser kernel, accumulated over all systems
  * while timing is on (aqs_set_kernel_timing(1)); pair visits count one atom

@@ -105,6 +105,9 @@ _SIGS = {
     "aqs_set_box": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "aqs_energy_forces": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p,
                                     C.POINTER(C.c_double)]),
+    "aqs_energy_forces_noalloc": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_void_p,
+                                            C.POINTER(C.c_double), C.POINTER(aqs_potential),
+                                            C.c_void_p, C.c_void_p, C.c_void_p]),
     "aqs_set_kernel_timing": (None, [C.c_int]),
     "aqs_get_kernel_stats": (None, [C.POINTER(aqs_kernel_stats)]),
     "aqs_reset_kernel_stats": (None, []),
