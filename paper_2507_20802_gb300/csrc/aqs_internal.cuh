@@ -46,16 +46,29 @@ struct RepGeom {
   double tilt_b;   // H[0][1] when the list was built
 };
 
+// Minimiser state of one replica, written by the kernel.  A replica runs a
+// "job" of nsteps fine steps (affine dgamma, then FIRE to convergence); the
+// first step skips the affine map when first_noaffine is set (the level-II
+// chains' first minimisation).  A launch may stop inside a job (list rebuild,
+// iteration budget) and the next launch resumes it.
 struct RepState {
   double dt, alpha;
   double E, fmax, tau;
-  int64_t iters;    // FIRE position updates since the minimisation started
-  int64_t evals64;  // FP64 force evaluations since the minimisation started
-  int64_t evals32;  // FP32 (relative) force evaluations since the minimisation started
+  double tilt;      // current H[0][1] (authoritative; the host mirrors it)
+  double tilt_b;    // H[0][1] when the list was built (host-written)
+  double dgamma;    // fine increment of the job
+  int64_t iters;    // FIRE position updates of the current step
+  int64_t evals64;  // FP64 force evaluations of the current step
+  int64_t evals32;  // FP32 (relative) force evaluations of the current step
+  int64_t acc_iters, acc64, acc32;  // monotonic counters over all launches
+  int64_t step;     // steps of the job completed
+  int64_t nsteps;   // steps of the job
   int npos;
-  int status;       // aqs_status; kStatusRebuild while waiting for a rebuild
-  int fresh;        // 1: next minimise call starts FIRE from scratch
-  int nlist_over;   // list overflow seen at the last build
+  int status;       // aqs_status; kStatusRebuild / kStatusRunning while unfinished
+  int phase;        // 0: next step not started, 1: FIRE in progress
+  int first_noaffine;
+  int want_snap;    // write the positions after the first (no-affine) step
+  int pad;
 };
 
 constexpr int kStatusRebuild = 100;

@@ -13,7 +13,7 @@ struct MinArgs {
   double* fref;     // [D][ntot] (mixed)
   double* dl;       // [D][ntot] delta (mixed)
   double* xs;       // [D][ntot] positions at the start of the minimisation
-  const double* xb; // [D][ntot] positions at the last list build (affinely mapped)
+  double* xb;       // [D][ntot] positions at the last list build (affinely mapped)
   const int32_t* type;
   const int32_t* cell;
   const uint32_t* nb;
@@ -24,6 +24,11 @@ struct MinArgs {
   FireDev fire;
   double skin, rlist;
   int64_t launch_budget;  // FIRE iterations per launch before yielding
+  double* rec;            // [R][rec_stride][5] per-step records (nullable)
+  int64_t rec_stride;
+  double* snap;           // [R][snap_stride] caller-order positions after step 0 (nullable)
+  int64_t snap_stride;
+  const int32_t* perm;    // [ntot] caller index of every atom
   int npc_launch;         // shared-memory stride (largest npc of the launch)
   int nrep_launch;        // largest replica of the launch (staged positions)
 };

@@ -155,8 +155,10 @@ constexpr int kModeEval64 = 0, kModeDev = 1;
 struct Ctl {
   double dt, ratio, keep;     // FIRE step after an FP64 evaluation
   float dtf, ratiof, keepf;   // the same in FP32 for the FP32 update
-  int move, mode, stop, reset, want_e, was64;
+  int move, mode, stop, reset, want_e, was64, status;
 };
+
+constexpr int kRecFields = 5;  // per converged step: E, tau, D_k, FIRE iterations, FP64 evaluations
 
 // Compensated ("float-float") sum on the FP32 pipe: TwoSum of Knuth (TAOCP
 // vol. 2, 4.2.2) followed by renormalisation (Dekker 1971).  The pair
@@ -220,44 +222,55 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   __shared__ Pub<D>* rpub[kMaxCluster];
   __shared__ double* rred[kMaxCluster];
   __shared__ Ctl ctl;
+  __shared__ double shv[4];
   __shared__ unsigned need;  // MEM 2: bit r set if rank r owns neighbours of this CTA
   if (tid == 0) need = 0u;
   __syncthreads();
 
-  // ---- set-up: tables, remote bases, list rows, FIRE state ----
+  // ---- set-up: geometry (tilt from the kernel-written state), tables ----
   double H[9];
 #pragma unroll
   for (int k = 0; k < 9; k++) H[k] = g.H[k];
+  H[1] = st->tilt;
   const int ncode = D == 2 ? 9 : 27;
-  if (tid < ncode) {
-    double o[3];
-    cell_offset<D>(H, g.nc, tid, o);
-    for (int k = 0; k < D; k++) {
-      off64[tid * 3 + k] = o[k];
-      off32[tid * 3 + k] = (float)o[k];
+  auto make_tables = [&]() {
+    if (tid < ncode) {
+      double o[3];
+      cell_offset<D>(H, g.nc, tid, o);
+      for (int k = 0; k < D; k++) {
+        off64[tid * 3 + k] = o[k];
+        off32[tid * 3 + k] = (float)o[k];
+      }
     }
-  }
+  };
+  make_tables();
   for (int k = tid; k < A.nt * A.nt; k += nthr) coef[k] = A.coef[k];
   if (tid < C) {
     rpub[tid] = cl.map_shared_rank(pub, tid);
     rred[tid] = cl.map_shared_rank(red, tid);
   }
   const FireDev fp = A.fire;
-  const bool fresh = st->fresh != 0;
-  // FIRE scalars: meaningful in thread 0 only
-  double dt = fresh ? fp.dt0 : st->dt;
-  double alpha = fresh ? fp.alpha0 : st->alpha;
+  // ---- the replica's job: nsteps fine steps (affine dgamma + minimisation) ----
+  int64_t step = st->step;
+  const int64_t nsteps = st->nsteps;
+  const bool first_noaffine = st->first_noaffine != 0;
+  const bool want_snap = st->want_snap != 0;
+  const double dgam = st->dgamma;
+  int phase = st->phase;  // 0: the next step has not started, 1: FIRE in progress
+  const double tilt_b = st->tilt_b;
+  // FIRE scalars (meaningful in thread 0 only)
+  double dt = st->dt, alpha = st->alpha;
   float dtf = (float)dt, alphaf = (float)alpha;  // mixed mode keeps these in FP32
-  int npos = fresh ? 0 : st->npos;
-  int64_t iters = fresh ? 0 : st->iters;
-  int64_t evals = fresh ? 0 : st->evals64;
-  int64_t evals32 = fresh ? 0 : st->evals32;
-  const int64_t iters0 = iters;
-  const double gamma_term = fabs(H[0 * D + 1] - g.tilt_b) / H[1 * D + 1] * A.rlist;
+  int npos = st->npos;
+  int64_t iters = st->iters, evals = st->evals64, evals32 = st->evals32;
+  int64_t launch_iters = 0;
+  int64_t acc_it = st->acc_iters, acc64 = st->acc64, acc32 = st->acc32;
   const double vol = D == 2 ? H[0] * H[3] : H[0] * H[4] * H[8];
   bool want_e = MIXED;  // mixed: every FP64 evaluation also gives E and tau
   float wmaxf = 0.0f;   // max |x_ref - x_b| at the last FP64 evaluation (mixed)
-  const float gamma_termf = (float)gamma_term, skinf = (float)A.skin;
+  double gamma_term = 0.0;
+  float gamma_termf = 0.0f;
+  const float skinf = (float)A.skin;
   const float tolf = (float)fp.tol, ratio_f = (float)fp.ref_ratio, dmax_f = (float)fp.ref_dmax;
   const float f_incf = (float)fp.f_inc, f_decf = (float)fp.f_dec, f_alphaf = (float)fp.f_alpha;
   const float dt_maxf = (float)fp.dt_max, dt_minf = (float)fp.dt_min, alpha0f = (float)fp.alpha0;
@@ -275,13 +288,8 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
     if (li < cnt) {
       int64_t gi = base + li;
       ty[k] = A.type[gi];
-      for (int c = 0; c < D; c++) {
-        if (fresh) {
-          A.v[c * N + gi] = 0.0;
-          A.xs[c * N + gi] = A.x[c * N + gi];
-        }
-        if (MIXED) v32[k][c] = (float)A.v[c * N + gi];
-      }
+      if (MIXED && phase == 1)
+        for (int c = 0; c < D; c++) v32[k][c] = (float)A.v[c * N + gi];
       if (LSM) {
         const int nn = A.nnb[gi];
         const uint32_t* row = A.nb + g.nb_off + lo + li;
@@ -305,26 +313,99 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   };
   // MEM 2: copy the records of the other CTAs that own neighbours (16-byte words)
   auto stage = [&]() {
-    constexpr int W = sizeof(Pub<D>) / 16;
+    constexpr int Wd = sizeof(Pub<D>) / 16;
     for (int r = 0; r < C; r++) {
       if (r == rank || !((need >> r) & 1u)) continue;
       const int cr = max(0, min(npc, n - r * npc));
       const uint4* src = reinterpret_cast<const uint4*>(rpub[r] + r * npc);
       uint4* dst = reinterpret_cast<uint4*>(pub + r * npc);
-      for (int w = tid; w < cr * W; w += nthr) dst[w] = src[w];
+      for (int w = tid; w < cr * Wd; w += nthr) dst[w] = src[w];
     }
   };
-#pragma unroll
-  for (int k = 0; k < APT; k++)
-    if (tid + k * nthr < cnt) publish64(k);
-  int mode = kModeEval64;
-  cl.sync();
+  // cluster-wide FP64 reduction of nv (<= 4) values; identical result in every CTA
+  auto cluster_reduce = [&](double* v, int nv, bool is_max) {
+    for (int m = 0; m < nv; m++)
+      for (int o = 16; o > 0; o >>= 1) {
+        double t = __shfl_xor_sync(0xffffffffu, v[m], o);
+        v[m] = is_max ? fmax(v[m], t) : v[m] + t;
+      }
+    if (lane == 0)
+      for (int m = 0; m < nv; m++) wred[warp * kNumRed + m] = v[m];
+    __syncthreads();
+    if (warp == 0) {
+      for (int m = 0; m < nv; m++) {
+        double t = lane < nwarp ? wred[lane * kNumRed + m] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+          double u = __shfl_xor_sync(0xffffffffu, t, o);
+          t = is_max ? fmax(t, u) : t + u;
+        }
+        if (lane == 0) red[m] = t;
+      }
+    }
+    cl.sync();
+    if (warp == 0) {
+      for (int m = 0; m < nv; m++) {
+        double t = lane < C ? rred[lane][m] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+          double u = __shfl_xor_sync(0xffffffffu, t, o);
+          t = is_max ? fmax(t, u) : t + u;
+        }
+        if (lane == 0) shv[m] = t;
+      }
+    }
+    cl.sync();  // every CTA has read the partials before they are reused
+    for (int m = 0; m < nv; m++) v[m] = shv[m];
+  };
 
   for (;;) {
-    if (MEM == 2) {
-      stage();
-      __syncthreads();
+    if (step >= nsteps) {
+      status = AQS_OK;
+      break;
     }
+    if (phase == 0) {
+      // ---- start of a fine step: affine map (Eq. 16) unless it is the
+      // level-II chain's first minimisation, then a fresh FIRE ----
+      const bool affine = !(step == 0 && first_noaffine);
+#pragma unroll
+      for (int k = 0; k < APT; k++) {
+        int li = tid + k * nthr;
+        if (li >= cnt) continue;
+        int64_t gi = base + li;
+        if (affine) {
+          A.x[gi] = fma(dgam, A.x[N + gi], A.x[gi]);
+          A.xb[gi] = fma(dgam, A.xb[N + gi], A.xb[gi]);
+        }
+        for (int c = 0; c < D; c++) {
+          A.v[c * N + gi] = 0.0;
+          A.xs[c * N + gi] = A.x[c * N + gi];
+          v32[k][c] = 0.0f;
+          d32[k][c] = 0.0f;
+        }
+      }
+      if (affine) H[1] = fma(dgam, H[D + 1], H[1]);
+      dt = fp.dt0;
+      alpha = fp.alpha0;
+      dtf = (float)dt;
+      alphaf = (float)alpha;
+      npos = 0;
+      iters = evals = evals32 = 0;
+      want_e = MIXED;
+      phase = 1;
+      make_tables();
+    }
+    gamma_term = fabs(H[1] - tilt_b) / H[D + 1] * A.rlist;
+    gamma_termf = (float)gamma_term;
+#pragma unroll
+    for (int k = 0; k < APT; k++)
+      if (tid + k * nthr < cnt) publish64(k);
+    int mode = kModeEval64;
+    cl.sync();
+
+    for (;;) {
+      if (MEM == 2) {
+        stage();
+        __syncthreads();
+      }
     // ================= force phase =================
     double r[kNumRed];
 #pragma unroll
@@ -525,6 +606,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         bool finite;
         if (was64) {
           evals++;
+          acc64++;
           fmx = sqrt(T[0]);
           fm = (float)fmx;
           finite = (T[0] < INFINITY) && (T[2] < INFINITY) && (T[1] == T[1]) &&
@@ -536,6 +618,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
           V2 = (float)T[3];
         } else {
           evals32++;
+          acc32++;
           fm = sqrtf(Tf[0]);
           finite = (Tf[0] < INFINITY) && (Tf[2] < INFINITY) && (Tf[1] == Tf[1]);
           umax = wmaxf + sqrtf(Tf[4]);
@@ -559,7 +642,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         } else if (iters >= fp.max_iter) {
           status = AQS_ERR_NOT_CONVERGED;
           stop = true;
-        } else if (iters - iters0 >= A.launch_budget) {
+        } else if (launch_iters >= A.launch_budget) {
           stop = true;  // status stays "running": the next launch resumes
         }
         c.stop = stop;
@@ -597,12 +680,14 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
             c.keepf = 1.0f - alphaf;
           }
           iters++;
+          acc_it++;
           mode = (was64 && fmx > kBigForce) ? kModeEval64 : kModeDev;
         } else if (!stop) {
           mode = kModeEval64;
         }
       } else {
         evals++;
+        acc64++;
         fmx = sqrt(T[0]);
         const bool finite = (T[0] < INFINITY) && (T[2] < INFINITY) && (T[1] == T[1]) &&
                             (!want_e || (fabs(T[6]) < INFINITY));
@@ -626,7 +711,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         } else if (iters >= fp.max_iter) {
           status = AQS_ERR_NOT_CONVERGED;
           stop = true;
-        } else if (iters - iters0 >= A.launch_budget) {
+        } else if (launch_iters >= A.launch_budget) {
           stop = true;
         }
         c.stop = stop;
@@ -654,6 +739,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
           c.ratio = alpha * sqrt(vn2 / F2);
           c.keep = 1.0 - alpha;
           iters++;
+          acc_it++;
         }
         mode = kModeEval64;
         c.dtf = c.ratiof = 0.f;
@@ -662,12 +748,15 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
       c.mode = mode;
       c.want_e = want_e;
       c.was64 = was64;
+      c.status = status;
       ctl = c;
     }
     __syncthreads();
     const Ctl c = ctl;
     mode = c.mode;
     want_e = c.want_e;
+    status = c.status;
+    if (c.move) launch_iters++;  // uniform in every thread
     if (c.stop) break;
 
     if (c.move) {
@@ -788,20 +877,91 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         publish64(k);
       }
     }
-    cl.sync();  // (B) new positions visible; partial slots free again
+      cl.sync();  // (B) new positions visible; partial slots free again
+    }
+    // materialise x = x_ref + delta (mixed)
+    if (MIXED) {
+#pragma unroll
+      for (int k = 0; k < APT; k++) {
+        int li = tid + k * nthr;
+        if (li >= cnt) continue;
+        int64_t gi = base + li;
+        for (int c = 0; c < D; c++) {
+          A.x[c * N + gi] += (double)d32[k][c];
+          d32[k][c] = 0.0f;
+        }
+      }
+    }
+    if (status != AQS_OK) break;  // rebuild, budget or error: the next launch resumes
+    // ---- step converged: non-affine displacement D_k, records, snapshot ----
+    {
+      double sv[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int k = 0; k < APT; k++) {
+        int li = tid + k * nthr;
+        if (li >= cnt) continue;
+        int64_t gi = base + li;
+        double d[3];
+        for (int c = 0; c < D; c++) d[c] = A.x[c * N + gi] - A.xs[c * N + gi];
+        min_image<D>(H, d);
+        for (int c = 0; c < D; c++) sv[c] += d[c];
+      }
+      cluster_reduce(sv, D, false);
+      double mx[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int k = 0; k < APT; k++) {
+        int li = tid + k * nthr;
+        if (li >= cnt) continue;
+        int64_t gi = base + li;
+        double d[3], s2 = 0.0;
+        for (int c = 0; c < D; c++) d[c] = A.x[c * N + gi] - A.xs[c * N + gi];
+        min_image<D>(H, d);
+        for (int c = 0; c < D; c++) {
+          double u = d[c] - sv[c] / n;
+          s2 += u * u;
+        }
+        mx[0] = fmax(mx[0], s2);
+      }
+      cluster_reduce(mx, 1, true);
+      if (rank == 0 && tid == 0 && A.rec) {
+        double* rec = A.rec + ((int64_t)ri * A.rec_stride + step) * kRecFields;
+        rec[0] = E;
+        rec[1] = W;
+        rec[2] = sqrt(mx[0]);
+        rec[3] = (double)iters;
+        rec[4] = (double)evals;
+      }
+      if (step == 0 && first_noaffine && want_snap && A.snap) {
+        double* sp = A.snap + (int64_t)ri * A.snap_stride;
+#pragma unroll
+        for (int k = 0; k < APT; k++) {
+          int li = tid + k * nthr;
+          if (li >= cnt) continue;
+          int64_t gi = base + li;
+          const int u = A.perm[gi];
+          for (int c = 0; c < D; c++) sp[(int64_t)u * D + c] = A.x[c * N + gi];
+        }
+      }
+    }
+    step++;
+    phase = 0;
+    status = kStatusRunning;
+    if (step >= nsteps) {
+      status = AQS_OK;
+      break;
+    }
+    if (launch_iters >= A.launch_budget) break;  // yield; the next launch starts the step
+    cl.sync();  // everybody is done with this step before the next one publishes
   }
 
-  // ---- exit: materialise x = x_ref + delta, keep v, store the FIRE state ----
-  if (MIXED) {
+  // ---- exit: keep v for a resumed minimisation, store the job state ----
+  if (MIXED && phase == 1) {
 #pragma unroll
     for (int k = 0; k < APT; k++) {
       int li = tid + k * nthr;
       if (li >= cnt) continue;
       int64_t gi = base + li;
-      for (int cc = 0; cc < D; cc++) {
-        A.x[cc * N + gi] += (double)d32[k][cc];
-        A.v[cc * N + gi] = (double)v32[k][cc];
-      }
+      for (int c = 0; c < D; c++) A.v[c * N + gi] = (double)v32[k][c];
     }
   }
   if (rank == 0 && tid == 0) {
@@ -811,9 +971,14 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
     st->iters = iters;
     st->evals64 = evals;
     st->evals32 = evals32;
+    st->acc_iters = acc_it;
+    st->acc64 = acc64;
+    st->acc32 = acc32;
     st->status = status;
     st->fmax = fmx;
-    st->fresh = 0;
+    st->step = step;
+    st->phase = phase;
+    st->tilt = H[1];
     if (status == AQS_OK) {
       st->E = E;
       st->tau = W;

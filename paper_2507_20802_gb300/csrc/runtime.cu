@@ -95,6 +95,10 @@ struct aqs_system {
   double* d_partial = nullptr;
   int64_t* d_i64 = nullptr;  // small scratch (copy offsets)
   double* d_shift = nullptr;
+  // per-step job records and first-step snapshots
+  double* d_rec = nullptr;
+  int64_t rec_cap = 0;
+  double* d_snap = nullptr;
   // two-level stepping resources
   aqs_system* chains = nullptr;
   double* snap = nullptr;
@@ -199,7 +203,20 @@ aqs_status download_state(aqs_system* s) {
   CUDA_TRY(cudaMemcpyAsync(s->st.data(), s->d_state, sizeof(RepState) * s->R,
                            cudaMemcpyDeviceToHost, s->stream));
   CUDA_TRY(cudaStreamSynchronize(s->stream));
+  // the kernels own the tilt while they shear; mirror it into the geometry
+  bool changed = false;
+  for (int r = 0; r < s->R; r++)
+    if (s->geom[r].H[1] != s->st[r].tilt) {
+      s->geom[r].H[1] = s->st[r].tilt;
+      changed = true;
+    }
+  if (changed) AQS_TRY(upload_geom(s));
   return AQS_OK;
+}
+
+// after the host changed a cell: the kernel-side copy of the tilt follows
+void sync_tilt_to_state(aqs_system* s) {
+  for (int r = 0; r < s->R; r++) s->st[r].tilt = s->geom[r].H[1];
 }
 
 BuildArgs build_args(aqs_system* s) {
@@ -319,8 +336,13 @@ aqs_status rebuild(aqs_system* s, const std::vector<uint8_t>& flags, int depth =
     }
   }
   for (int r = 0; r < s->R; r++)
-    if (flags[r]) s->geom[r].tilt_b = s->geom[r].H[0 * D + 1];
+    if (flags[r]) {
+      s->geom[r].tilt_b = s->geom[r].H[0 * D + 1];
+      s->st[r].tilt_b = s->geom[r].tilt_b;
+      s->st[r].tilt = s->geom[r].H[0 * D + 1];
+    }
   AQS_TRY(upload_geom(s));
+  AQS_TRY(upload_state(s));
   return AQS_OK;
 }
 
@@ -395,9 +417,14 @@ MinArgs min_args(aqs_system* s, const aqs_fire_params* f) {
   a.fire = fire_dev(f);
   a.skin = s->skin;
   a.rlist = s->rlist;
-  a.launch_budget = 4096;
+  a.launch_budget = 2048;
   a.npc_launch = 0;
   a.nrep_launch = 0;
+  a.rec = s->d_rec;
+  a.rec_stride = s->rec_cap;
+  a.snap = s->d_snap;
+  a.snap_stride = (int64_t)s->dim * s->nmax;
+  a.perm = s->perm;
   return a;
 }
 
@@ -427,28 +454,67 @@ aqs_status nonaffine(aqs_system* s, const std::vector<int>& reps, std::vector<do
   return AQS_OK;
 }
 
-// Minimise the replicas with mask[r]; fills res[r] for those.
-aqs_status minimize_impl(aqs_system* s, const aqs_fire_params* f, const std::vector<uint8_t>& mask,
-                         aqs_min_result* res) {
+// Per-replica job: nsteps fine steps of increment dgamma (affine map, then
+// FIRE to convergence); first_noaffine skips the map of the first step and
+// want_snap stores the caller-order positions after that first step.
+struct Job {
+  int64_t nsteps = 0;
+  double dgamma = 0.0;
+  int first_noaffine = 0;
+  int want_snap = 0;
+};
+
+struct JobOut {
+  std::vector<double> rec;  // [R][nsteps_max][5]: E, tau, D_k, iterations, FP64 evaluations
+  int64_t stride = 0;
+  std::vector<int64_t> rebuilds;
+};
+
+aqs_status ensure_records(aqs_system* s, int64_t nsteps, bool snap) {
+  if (nsteps > s->rec_cap) {
+    dfree(s, s->d_rec);
+    s->rec_cap = std::max<int64_t>(nsteps, 2 * s->rec_cap);
+    AQS_TRY(alloc_arr(s, &s->d_rec, (size_t)s->R * s->rec_cap * 5));
+  }
+  if (snap && !s->d_snap) AQS_TRY(alloc_arr(s, &s->d_snap, (size_t)s->R * s->dim * s->nmax));
+  return AQS_OK;
+}
+
+// Runs the jobs of the replicas with jobs[r].nsteps > 0 to completion in
+// persistent launches (one per cluster size and pass); between passes only
+// list rebuilds and budget yields are handled on the host.
+aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<Job>& jobs,
+                    JobOut* out) {
+  int64_t maxsteps = 0;
+  bool snap = false;
   std::vector<int> todo;
   for (int r = 0; r < s->R; r++)
-    if (mask[r]) {
+    if (jobs[r].nsteps > 0) {
       todo.push_back(r);
-      s->st[r].fresh = 1;
-      s->st[r].status = kStatusRunning;
+      maxsteps = std::max(maxsteps, jobs[r].nsteps);
+      snap = snap || jobs[r].want_snap;
+      RepState& t = s->st[r];
+      t.nsteps = jobs[r].nsteps;
+      t.dgamma = jobs[r].dgamma;
+      t.first_noaffine = jobs[r].first_noaffine;
+      t.want_snap = jobs[r].want_snap;
+      t.step = 0;
+      t.phase = 0;
+      t.status = kStatusRunning;
+      t.tilt = s->geom[r].H[1];
     }
   if (todo.empty()) return AQS_OK;
+  AQS_TRY(ensure_records(s, maxsteps, snap));
   AQS_TRY(upload_state(s));
   std::vector<int64_t> rebuilds(s->R, 0);
   std::vector<int> order_work;
-  for (int64_t pass = 0; pass < 10000000 && !todo.empty(); pass++) {
-    // group the pending replicas by cluster size; one launch per group
+  for (int64_t pass = 0; pass < 100000000 && !todo.empty(); pass++) {
     std::vector<int> Cs;
     for (int r : todo) Cs.push_back(s->geom[r].C);
     std::sort(Cs.begin(), Cs.end());
     Cs.erase(std::unique(Cs.begin(), Cs.end()), Cs.end());
     order_work.clear();
-    std::vector<std::pair<int, int>> groups;  // (start, count)
+    std::vector<std::pair<int, int>> groups;
     for (int C : Cs) {
       int start = (int)order_work.size();
       for (int r : todo)
@@ -460,8 +526,6 @@ aqs_status minimize_impl(aqs_system* s, const aqs_fire_params* f, const std::vec
     MinArgs a = min_args(s, f);
     const bool timing = g_timing.load() != 0;
     std::vector<RepState> before(s->st);
-    for (int r : todo)
-      if (s->st[r].fresh) before[r].evals32 = before[r].evals64 = before[r].iters = 0;
     if (timing) CUDA_TRY(cudaEventRecord(s->ev0, s->stream));
     for (size_t gi = 0; gi < groups.size(); gi++) {
       int C = Cs[gi];
@@ -482,55 +546,77 @@ aqs_status minimize_impl(aqs_system* s, const aqs_fire_params* f, const std::vec
       g_stats.launches += (int64_t)groups.size();
       g_stats.kernel_ms += ms;
       for (int r : todo) {
-        int64_t d32 = s->st[r].evals32 - before[r].evals32;
-        int64_t d64 = s->st[r].evals64 - before[r].evals64;
+        int64_t d32 = s->st[r].acc32 - before[r].acc32;
+        int64_t d64 = s->st[r].acc64 - before[r].acc64;
+        int64_t dit = s->st[r].acc_iters - before[r].acc_iters;
         g_stats.evals32 += d32;
         g_stats.evals64 += d64;
         g_stats.pairs32 += d32 * s->nnb_sum[r];
         g_stats.pairs64 += d64 * s->nnb_sum[r];
-        g_stats.atom_iters += (s->st[r].iters - before[r].iters) * s->n[r];
+        g_stats.atom_iters += dit * s->n[r];
       }
     }
     std::vector<uint8_t> flags(s->R, 0);
     std::vector<int> next;
     for (int r : todo) {
-      if (s->st[r].status == kStatusRebuild) {
+      const int st = s->st[r].status;
+      if (st == kStatusRebuild) {
         flags[r] = 1;
         rebuilds[r]++;
       }
-      if (s->st[r].status == kStatusRebuild || s->st[r].status == kStatusRunning) next.push_back(r);
+      if (st == kStatusRebuild || st == kStatusRunning) next.push_back(r);
     }
-    if (!next.empty()) AQS_TRY(rebuild(s, flags));
+    if (!next.empty() && std::count(flags.begin(), flags.end(), 1) > 0) AQS_TRY(rebuild(s, flags));
     todo.swap(next);
   }
-  if (!todo.empty()) return fail(AQS_ERR_TIMEOUT, "minimiser kept asking for list rebuilds");
-  std::vector<int> reps;
-  for (int r = 0; r < s->R; r++)
-    if (mask[r]) reps.push_back(r);
-  std::vector<double> na;
-  AQS_TRY(nonaffine(s, reps, na));
+  if (!todo.empty()) return fail(AQS_ERR_TIMEOUT, "minimiser jobs did not finish");
+  if (out) {
+    out->stride = s->rec_cap;
+    out->rec.assign((size_t)s->R * s->rec_cap * 5, 0.0);
+    CUDA_TRY(cudaMemcpyAsync(out->rec.data(), s->d_rec, sizeof(double) * out->rec.size(),
+                             cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    out->rebuilds = rebuilds;
+  }
   aqs_status first = AQS_OK;
-  for (size_t k = 0; k < reps.size(); k++) {
-    int r = reps[k];
+  for (int r = 0; r < s->R; r++) {
+    if (jobs[r].nsteps <= 0) continue;
     const RepState& t = s->st[r];
-    if (res) {
-      aqs_min_result& o = res[r];
-      o.iters = t.iters;
-      o.evals64 = t.evals64;
-      o.rebuilds = rebuilds[r];
-      o.energy = t.E;
-      o.fmax = t.fmax;
-      o.tau = t.tau;
-      o.nonaffine = na[k];
-      o.status = t.status;
-    }
     if (t.status != AQS_OK && first == AQS_OK) {
       first = (aqs_status)t.status;
-      fail(first, "replica %d: minimiser status %d after %lld iterations (fmax %.3g)", r,
-           t.status, (long long)t.iters, t.fmax);
+      fail(first, "replica %d: minimiser status %d at step %lld after %lld iterations (fmax %.3g)",
+           r, t.status, (long long)t.step, (long long)t.iters, t.fmax);
     }
   }
   return first;
+}
+
+// One minimisation (a one-step job without affine map) of the masked replicas.
+aqs_status minimize_impl(aqs_system* s, const aqs_fire_params* f, const std::vector<uint8_t>& mask,
+                         aqs_min_result* res) {
+  std::vector<Job> jobs(s->R);
+  for (int r = 0; r < s->R; r++)
+    if (mask[r]) {
+      jobs[r].nsteps = 1;
+      jobs[r].first_noaffine = 1;
+    }
+  JobOut out;
+  aqs_status st = run_jobs(s, f, jobs, &out);
+  for (int r = 0; r < s->R; r++) {
+    if (!mask[r] || !res) continue;
+    const RepState& t = s->st[r];
+    const double* rec = &out.rec[(size_t)r * out.stride * 5];
+    aqs_min_result& o = res[r];
+    o.iters = t.status == AQS_OK ? (int64_t)rec[3] : t.iters;
+    o.evals64 = t.status == AQS_OK ? (int64_t)rec[4] : t.evals64;
+    o.rebuilds = out.rebuilds.empty() ? 0 : out.rebuilds[r];
+    o.energy = t.status == AQS_OK ? rec[0] : 0.0;
+    o.fmax = t.fmax;
+    o.tau = t.status == AQS_OK ? rec[1] : 0.0;
+    o.nonaffine = t.status == AQS_OK ? rec[2] : 0.0;
+    o.status = t.status;
+  }
+  return st;
 }
 
 aqs_status affine_impl(aqs_system* s, const std::vector<double>& dg) {
@@ -543,6 +629,8 @@ aqs_status affine_impl(aqs_system* s, const std::vector<double>& dg) {
   }
   if (!any) return AQS_OK;
   AQS_TRY(upload_geom(s));
+  sync_tilt_to_state(s);
+  AQS_TRY(upload_state(s));
   CUDA_TRY(cudaMemcpyAsync(s->d_dg, dg.data(), sizeof(double) * s->R, cudaMemcpyHostToDevice,
                            s->stream));
   CUDA_TRY(launch_affine(s->x, s->xb, s->d_rep_of, s->d_dg, s->ntot, s->stream));
@@ -631,7 +719,6 @@ aqs_status init_system(aqs_system* s, int dim, int R, const int64_t* n, const aq
     C = std::max(1, std::min(C, kMaxCluster));
     g.C = C;
     g.npc = (int)((n[r] + C - 1) / C);
-    s->st[r].fresh = 1;
     s->st[r].status = AQS_OK;
   }
   AQS_TRY(alloc_system(s));
@@ -934,21 +1021,33 @@ aqs_status aqs_minimize(aqs_system* s, const aqs_fire_params* f, const uint8_t* 
 aqs_status aqs_run_sequential(aqs_system* s, const aqs_fire_params* f, double dgamma,
                               int64_t n_steps, double* energy, double* tau, int64_t* fire_iters,
                               double* nonaffine_out) {
-  if (!s || !f || n_steps < 0) return fail(AQS_ERR_INVALID_ARG, "bad argument");
-  std::vector<double> dg(s->R, dgamma);
-  std::vector<uint8_t> all(s->R, 1);
-  std::vector<aqs_min_result> res(s->R);
-  for (int64_t k = 0; k < n_steps; k++) {
-    AQS_TRY(aqs_affine_shear(s, dg.data()));
-    AQS_TRY(minimize_impl(s, f, all, res.data()));
-    for (int r = 0; r < s->R; r++) {
-      size_t i = (size_t)k * s->R + r;
-      if (energy) energy[i] = res[r].energy;
-      if (tau) tau[i] = res[r].tau;
-      if (fire_iters) fire_iters[i] = res[r].iters;
-      if (nonaffine_out) nonaffine_out[i] = res[r].nonaffine;
-    }
+  if (!s || !f || n_steps < 0 || !std::isfinite(dgamma))
+    return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  if (n_steps == 0) return AQS_OK;
+  for (int r = 0; r < s->R; r++) {
+    double H[9];
+    std::memcpy(H, s->geom[r].H, sizeof(H));
+    H[1] += n_steps * dgamma * H[s->dim + 1];
+    double w[3];
+    cell_widths(s->dim, H, w);
+    if (!(s->rlist * 3.0 <= w[0])) return fail(AQS_ERR_BOX_TOO_SMALL, "tilt too large");
   }
+  std::vector<Job> jobs(s->R);
+  for (int r = 0; r < s->R; r++) {
+    jobs[r].nsteps = n_steps;
+    jobs[r].dgamma = dgamma;
+  }
+  JobOut out;
+  AQS_TRY(run_jobs(s, f, jobs, &out));
+  for (int64_t k = 0; k < n_steps; k++)
+    for (int r = 0; r < s->R; r++) {
+      const double* rec = &out.rec[((size_t)r * out.stride + k) * 5];
+      size_t i = (size_t)k * s->R + r;
+      if (energy) energy[i] = rec[0];
+      if (tau) tau[i] = rec[1];
+      if (fire_iters) fire_iters[i] = (int64_t)rec[3];
+      if (nonaffine_out) nonaffine_out[i] = rec[2];
+    }
   return AQS_OK;
 }
 
@@ -970,7 +1069,6 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
   out->n_log = 0;
   std::vector<double> cE((size_t)P * K), cT((size_t)P * K), cD((size_t)P * K);
   std::vector<int64_t> cI((size_t)P * K);
-  std::vector<aqs_min_result> res(P);
   int64_t n_cur = 0;
   const size_t per = (size_t)D * n;
   while (n_cur < p->n_steps && (p->max_iterations <= 0 || out->iterations < p->max_iterations)) {
@@ -986,38 +1084,32 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
       shift[i] = (double)i * K * p->dgamma;
     }
     AQS_TRY(copy_replicas(s, src, c, drs, shift));
-    // level II (Eq. 19): first F on every chain -> outgoing configurations
-    std::vector<uint8_t> mask(P, 0);
-    for (int i = 0; i < P_eff; i++) mask[i] = 1;
-    AQS_TRY(minimize_impl(c, f, mask, res.data()));
+    // level II (Eq. 19): chain i runs F once (its outgoing configuration,
+    // kept as a caller-order snapshot for i >= 1) and then K_i fine AQS
+    // steps, all inside persistent launches; chains never wait for each other
+    // between fine steps
+    std::vector<Job> jobs(P);
     for (int i = 0; i < P_eff; i++) {
-      out->fire_iters_total += res[i].iters;
-      out->evals64_total += res[i].evals64;
+      jobs[i].nsteps = 1 + Ki[i];
+      jobs[i].dgamma = p->dgamma;
+      jobs[i].first_noaffine = 1;
+      jobs[i].want_snap = i >= 1;
     }
-    for (int i = 1; i < P_eff; i++) AQS_TRY(gather_user(c, i, c->snap + per * i));
-    // K fine AQS steps on every chain (the shortened last chain drops out)
-    for (int k = 0; k < K; k++) {
-      std::vector<double> dg(P, 0.0);
-      std::vector<uint8_t> mk(P, 0);
-      bool any = false;
-      for (int i = 0; i < P_eff; i++)
-        if (k < Ki[i]) {
-          dg[i] = p->dgamma;
-          mk[i] = 1;
-          any = true;
-        }
-      if (!any) break;
-      AQS_TRY(affine_impl(c, dg));
-      AQS_TRY(minimize_impl(c, f, mk, res.data()));
-      for (int i = 0; i < P_eff; i++)
-        if (mk[i]) {
-          cE[(size_t)i * K + k] = res[i].energy;
-          cT[(size_t)i * K + k] = res[i].tau;
-          cI[(size_t)i * K + k] = res[i].iters;
-          cD[(size_t)i * K + k] = res[i].nonaffine;
-          out->fire_iters_total += res[i].iters;
-          out->evals64_total += res[i].evals64;
-        }
+    JobOut jo;
+    AQS_TRY(run_jobs(c, f, jobs, &jo));
+    for (int i = 0; i < P_eff; i++) {
+      const double* rec = &jo.rec[(size_t)i * jo.stride * 5];
+      out->fire_iters_total += (int64_t)rec[3];
+      out->evals64_total += (int64_t)rec[4];
+      for (int k = 0; k < Ki[i]; k++) {
+        const double* q = rec + (size_t)(k + 1) * 5;
+        cE[(size_t)i * K + k] = q[0];
+        cT[(size_t)i * K + k] = q[1];
+        cD[(size_t)i * K + k] = q[2];
+        cI[(size_t)i * K + k] = (int64_t)q[3];
+        out->fire_iters_total += (int64_t)q[3];
+        out->evals64_total += (int64_t)q[4];
+      }
     }
     // sequential equality check (Eq. 20): end of chain i-1 vs F(r^c_iK)
     std::vector<double> m(P_eff, 0.0);
@@ -1027,7 +1119,7 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
         AQS_TRY(gather_user(c, i - 1, c->ends + per * (i - 1)));
         CmpJob& J = jobs[i - 1];
         J.a = c->ends + per * (i - 1);
-        J.b = c->snap + per * i;
+        J.b = c->d_snap + (size_t)c->dim * c->nmax * i;
         J.sa = D;
         J.sc = 1;
         J.sb = D;
@@ -1125,8 +1217,6 @@ aqs_status aqs_get_positions(const aqs_system* s, int r, double* out) {
 aqs_status aqs_set_positions(aqs_system* s, int r, const double* pos) {
   if (!s || !pos || r < 0 || r >= s->R) return fail(AQS_ERR_INVALID_ARG, "bad argument");
   AQS_TRY(put_positions(s, r, pos));
-  s->st[r].fresh = 1;
-  AQS_TRY(upload_state(s));
   std::vector<uint8_t> flags(s->R, 0);
   flags[r] = 1;
   return rebuild(s, flags);
