@@ -168,23 +168,19 @@ void cell_widths(int D, const double* H, double* w) {
 // clusters are resident at once (so every chain advances in every wave);
 // otherwise the C with the most resident CTAs.  At least 32 atoms per CTA and
 // at most 4096.
+// Cluster size for R concurrently minimised replicas of n atoms: spread the
+// replicas over the 152 SMs (one CTA per SM), at most 16 CTAs per replica, at
+// least 32 atoms per CTA and at most 4096.  The cluster scheduler's own limit
+// is checked with the occupancy API; a size it cannot place is skipped.
 int auto_cluster(int dim, bool mixed, int R, int64_t n, int nt, int cap) {
-  int best = 1;
-  double best_score = -1.0;
-  for (int C = kMaxCluster; C >= 1; C--) {
+  int C = std::min(kMaxCluster, std::max(1, 152 / std::max(1, R)));
+  C = (int)std::min<int64_t>(C, std::max<int64_t>(1, n / 32));
+  while ((n + C - 1) / C > 4096 && C < kMaxCluster) C++;
+  for (; C > 1; C--) {
     int64_t npc = (n + C - 1) / C;
-    if (npc > 4096) break;
-    if (C > 1 && n / C < 32) continue;
-    int m = minimize_max_active_clusters(dim, mixed, C, (int)npc, (int)n, nt, cap);
-    if (m <= 0) continue;
-    if (m >= R) return C;
-    double score = (double)std::min(R, m) * C;
-    if (score > best_score) {
-      best_score = score;
-      best = C;
-    }
+    if (minimize_max_active_clusters(dim, mixed, C, (int)npc, (int)n, nt, cap) > 0) break;
   }
-  return best;
+  return C;
 }
 
 aqs_status upload_geom(aqs_system* s) {
@@ -565,6 +561,19 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
         rebuilds[r]++;
       }
       if (st == kStatusRebuild || st == kStatusRunning) next.push_back(r);
+    }
+    // fewer replicas left: give each a larger cluster (the list is rebuilt
+    // for the new owner layout; the FIRE state carries over)
+    if (s->C_override <= 0 && !next.empty() && next.size() < todo.size()) {
+      for (int r : next) {
+        int Cn = auto_cluster(s->dim, s->prec == AQS_MIXED, (int)next.size(), s->n[r], s->nt,
+                              s->cap);
+        if (Cn > s->geom[r].C) {
+          s->geom[r].C = Cn;
+          s->geom[r].npc = (int)((s->n[r] + Cn - 1) / Cn);
+          flags[r] = 1;
+        }
+      }
     }
     if (!next.empty() && std::count(flags.begin(), flags.end(), 1) > 0) AQS_TRY(rebuild(s, flags));
     todo.swap(next);
