@@ -223,6 +223,60 @@ aqs_status aqs_set_box(aqs_system* sys, int replica, const double* H);
 aqs_status aqs_energy_forces(aqs_system* sys, int replica, double* energy, double* forces,
                              double* tau);
 
+/* ---- learned warm start (2D) ----
+ * The paper names extrapolation of the minimiser's starting point as future
+ * work (Sec. 5).  A per-atom network predicts the non-affine displacement per
+ * unit strain u_i of the next increment from the atom's neighbour shell; the
+ * minimisation starts from F^(dgamma) r_k + dgamma u and FIRE finishes it.
+ *
+ * Features of atom i (aqs_warm_features): the minimum-image displacements to
+ * its 32 nearest atoms, nearest first (ties: lower caller index first), then a
+ * one-hot species code (width 66 in 2D; BF16 rows are padded with zeros to
+ * AQS_WARM_IN = 80).  Rows are in caller order; with replica = -1 the rows of
+ * replica r start at the sum of the sizes of the replicas before it.
+ * Network: 80 -> 128 -> 128 -> 128 -> 2, GELU on the hidden layers, BF16
+ * weights and activations on tensor cores, FP32 accumulation, FP32 master
+ * weights; loss 0.5/m sum (y - t)^2; AdamW (beta 0.9, 0.999, eps 1e-8).
+ * Parameter vector (aqs_warm_num_params floats): W1 (128 x 80), W2, W3
+ * (128 x 128), W4 (16 x 128, rows >= 2 zero), b1, b2, b3 (128), b4 (16). */
+#define AQS_WARM_IN 80
+typedef struct aqs_warm aqs_warm;
+int aqs_warm_num_params(void);
+/* Glorot-uniform weights from a SplitMix64 stream of `seed`, zero biases. */
+aqs_status aqs_warm_create(int dim, int n_types, uint64_t seed, void* stream, aqs_warm** out);
+void aqs_warm_destroy(aqs_warm* w);
+aqs_status aqs_warm_get_params(const aqs_warm* w, float* host_params);
+aqs_status aqs_warm_set_params(aqs_warm* w, const float* host_params); /* resets AdamW state */
+/* feat_bf16: device [rows][80]; feat_f64: device [rows][66] or NULL */
+aqs_status aqs_warm_features(aqs_system* sys, int replica, void* feat_bf16, double* feat_f64);
+/* out: device [rows][2] FP32 */
+aqs_status aqs_warm_predict(aqs_warm* w, const void* feat_bf16, int64_t rows, float* out);
+/* loss and its gradient (host, aqs_warm_num_params floats, nullable) for
+ * targets (device [rows][2] FP32) */
+aqs_status aqs_warm_loss_grad(aqs_warm* w, const void* feat_bf16, const float* target,
+                              int64_t rows, float* grad_host, double* loss);
+/* one AdamW step on the full-batch gradient of the given rows */
+aqs_status aqs_warm_train_step(aqs_warm* w, const void* feat_bf16, const float* target,
+                               int64_t rows, double lr, double weight_decay, double* loss);
+/* Training data from the method itself: n_steps sequential AQS steps of all
+ * replicas; before each step the features of the current minima, after it
+ * the per-atom non-affine displacement per unit strain (targets).
+ * feat_out: device [n_steps][N_tot][80] BF16; target_out: device
+ * [n_steps][N_tot][2] FP32. */
+aqs_status aqs_warm_collect(aqs_system* sys, const aqs_fire_params* fire, double dgamma,
+                            int64_t n_steps, void* feat_out, float* target_out);
+/* Sequential AQS with the learned start.  A step keeps it only if the
+ * minimum lies within `gate` (<= 0 selects 0.01 sigma) of both the learned
+ * start and the plain affine start (an elastic step, so both starts lie in one
+ * basin); otherwise the step is redone from the plain affine start, which
+ * defines the AQS path (Eq. 12).  Per-step outputs as aqs_run_sequential;
+ * used_warm[i] = 1 where the learned start was kept; fire_iters includes the
+ * iterations of a discarded attempt. */
+aqs_status aqs_run_sequential_warm(aqs_system* sys, const aqs_fire_params* fire, aqs_warm* w,
+                                   double dgamma, int64_t n_steps, double gate, double* energy,
+                                   double* tau, int64_t* fire_iters, double* nonaffine,
+                                   uint8_t* used_warm);
+
 /* ---- allocation-free evaluation ----
  * The paper has no counterpart: this entry point exists for callers that
  * must not allocate device memory (inside another library's fixed memory

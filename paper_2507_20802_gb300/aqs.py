@@ -105,6 +105,24 @@ _SIGS = {
     "aqs_set_box": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "aqs_energy_forces": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p,
                                     C.POINTER(C.c_double)]),
+    "aqs_warm_num_params": (C.c_int, []),
+    "aqs_warm_create": (C.c_int, [C.c_int, C.c_int, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "aqs_warm_destroy": (None, [C.c_void_p]),
+    "aqs_warm_get_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "aqs_warm_set_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "aqs_warm_features": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "aqs_warm_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "aqs_warm_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                     C.POINTER(C.c_float), C.POINTER(C.c_double)]),
+    "aqs_warm_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
+                                      C.c_double, C.POINTER(C.c_double)]),
+    "aqs_warm_collect": (C.c_int, [C.c_void_p, C.POINTER(aqs_fire_params), C.c_double, C.c_int64,
+                                   C.c_void_p, C.c_void_p]),
+    "aqs_run_sequential_warm": (C.c_int, [C.c_void_p, C.POINTER(aqs_fire_params), C.c_void_p,
+                                          C.c_double, C.c_int64, C.c_double,
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_uint8)]),
     "aqs_energy_forces_noalloc": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_void_p,
                                             C.POINTER(C.c_double), C.POINTER(aqs_potential),
                                             C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -302,6 +320,74 @@ def aqs_reset_kernel_stats():
     lib().aqs_reset_kernel_stats()
 
 
+# ------------------------------------------------------------ warm start
+WARM_IN = 80
+
+
+class Warm:
+    """The learned warm-start network (device weights); thin wrapper over the
+    aqs_warm_* calls.  Device buffers are torch tensors (memory only)."""
+
+    def __init__(self, dim=2, n_types=2, seed=0, stream=None):
+        self.dim, self.n_types = dim, n_types
+        h = C.c_void_p()
+        check(lib().aqs_warm_create(dim, n_types, seed, C.c_void_p(stream) if stream else None,
+                                    C.byref(h)))
+        self.h = h
+        self.n_params = lib().aqs_warm_num_params()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().aqs_warm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        p = np.zeros(self.n_params, np.float32)
+        check(lib().aqs_warm_get_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float))))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        check(lib().aqs_warm_set_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def predict(self, feat, out):
+        check(lib().aqs_warm_predict(self.h, _ptr(feat), feat.shape[0], _ptr(out)))
+        return out
+
+    def loss_grad(self, feat, target):
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_double()
+        check(lib().aqs_warm_loss_grad(self.h, _ptr(feat), _ptr(target), feat.shape[0],
+                                       g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)))
+        return loss.value, g
+
+    def train_step(self, feat, target, lr, weight_decay=0.0):
+        loss = C.c_double()
+        check(lib().aqs_warm_train_step(self.h, _ptr(feat), _ptr(target), feat.shape[0],
+                                        C.c_double(lr), C.c_double(weight_decay), C.byref(loss)))
+        return loss.value
+
+
+def unpack_params(p, dim=2, n_in=WARM_IN, hid=128, out_pad=16):
+    """Split the flat parameter vector into (weights, biases) lists."""
+    shapes = [(hid, n_in), (hid, hid), (hid, hid), (out_pad, hid)]
+    Ws, k = [], 0
+    for s in shapes:
+        Ws.append(p[k:k + s[0] * s[1]].reshape(s))
+        k += s[0] * s[1]
+    bs = []
+    for n in [hid, hid, hid, out_pad]:
+        bs.append(p[k:k + n])
+        k += n
+    return Ws, bs
+
+
 # ------------------------------------------------------------ convenience
 class System:
     """Owns one aqs_system.  ``pos`` (N_tot x d) and ``types`` may be numpy
@@ -375,6 +461,25 @@ class System:
     def parallel_step(self, dgamma, K, P, n_steps, fire=None, replica=0, **kw):
         return aqs_parallel_step(self.h, replica, fire or fire_params(), dgamma, K, P, n_steps,
                                  **kw)
+
+    def warm_features(self, feat_bf16, feat_f64=None, replica=-1):
+        check(lib().aqs_warm_features(self.h, replica, _ptr(feat_bf16), _ptr(feat_f64)))
+
+    def warm_collect(self, dgamma, n_steps, feat_out, target_out, fire=None):
+        check(lib().aqs_warm_collect(self.h, C.byref(fire or fire_params()), C.c_double(dgamma),
+                                     C.c_int64(n_steps), _ptr(feat_out), _ptr(target_out)))
+
+    def run_sequential_warm(self, warm, dgamma, n_steps, gate=0.0, fire=None):
+        R = self.R
+        E, tau, D = (np.zeros((n_steps, R)) for _ in range(3))
+        it = np.zeros((n_steps, R), dtype=np.int64)
+        used = np.zeros((n_steps, R), dtype=np.uint8)
+        check(lib().aqs_run_sequential_warm(self.h, C.byref(fire or fire_params()), warm.h,
+                                            C.c_double(dgamma), C.c_int64(n_steps),
+                                            C.c_double(gate), _dp(E), _dp(tau),
+                                            it.ctypes.data_as(C.POINTER(C.c_int64)), _dp(D),
+                                            used.ctypes.data_as(C.POINTER(C.c_uint8))))
+        return dict(E=E, tau=tau, iters=it, D=D, used=used)
 
     def mean_neighbours(self, replica=0):
         return lib().aqs_mean_neighbours(self.h, replica)

@@ -71,6 +71,10 @@ struct RepState {
   int pad;
 };
 
+// per converged step the kernel records: E, tau, D_k (from the affine start), FIRE
+// iterations, FP64 evaluations, max displacement from the minimisation's start
+constexpr int kRecFields = 6;
+
 constexpr int kStatusRebuild = 100;
 constexpr int kStatusRunning = 101;
 

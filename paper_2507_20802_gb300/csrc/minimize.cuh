@@ -29,6 +29,8 @@ struct MinArgs {
   double* snap;           // [R][snap_stride] caller-order positions after step 0 (nullable)
   int64_t snap_stride;
   const int32_t* perm;    // [ntot] caller index of every atom
+  const float* warm_u;    // [ntot][D] learned start displacement per unit strain, caller order
+                          // within each replica (nullable)
   int npc_launch;         // shared-memory stride (largest npc of the launch)
   int nrep_launch;        // largest replica of the launch (staged positions)
 };

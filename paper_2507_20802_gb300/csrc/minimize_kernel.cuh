@@ -158,7 +158,6 @@ struct Ctl {
   int move, mode, stop, reset, want_e, was64, status;
 };
 
-constexpr int kRecFields = 5;  // per converged step: E, tau, D_k, FIRE iterations, FP64 evaluations
 
 // Compensated ("float-float") sum on the FP32 pipe: TwoSum of Knuth (TAOCP
 // vol. 2, 4.2.2) followed by renormalisation (Dekker 1971).  The pair
@@ -374,6 +373,11 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         if (affine) {
           A.x[gi] = fma(dgam, A.x[N + gi], A.x[gi]);
           A.xb[gi] = fma(dgam, A.xb[N + gi], A.xb[gi]);
+          if (A.warm_u) {
+            // learned start: F r_k + dgamma u (caller-order prediction)
+            const float* u = A.warm_u + (g.off + A.perm[gi]) * D;
+            for (int c = 0; c < D; c++) A.x[c * N + gi] = fma(dgam, (double)u[c], A.x[c * N + gi]);
+          }
         }
         for (int c = 0; c < D; c++) {
           A.v[c * N + gi] = 0.0;
@@ -895,7 +899,10 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
     if (status != AQS_OK) break;  // rebuild, budget or error: the next launch resumes
     // ---- step converged: non-affine displacement D_k, records, snapshot ----
     {
-      double sv[4] = {0.0, 0.0, 0.0, 0.0};
+      // displacement from the start of the minimisation (d) and from the plain
+      // affine start (d + dgamma u when a learned start was used)
+      const bool warm = A.warm_u && !(step == 0 && first_noaffine);
+      double sv[4] = {0.0, 0.0, 0.0, 0.0}, sa[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
       for (int k = 0; k < APT; k++) {
         int li = tid + k * nthr;
@@ -905,24 +912,33 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         for (int c = 0; c < D; c++) d[c] = A.x[c * N + gi] - A.xs[c * N + gi];
         min_image<D>(H, d);
         for (int c = 0; c < D; c++) sv[c] += d[c];
+        if (warm) {
+          const float* u = A.warm_u + (g.off + A.perm[gi]) * D;
+          for (int c = 0; c < D; c++) sa[c] += d[c] + dgam * (double)u[c];
+        }
       }
       cluster_reduce(sv, D, false);
+      if (warm) cluster_reduce(sa, D, false);
       double mx[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
       for (int k = 0; k < APT; k++) {
         int li = tid + k * nthr;
         if (li >= cnt) continue;
         int64_t gi = base + li;
-        double d[3], s2 = 0.0;
+        double d[3], s2 = 0.0, a2 = 0.0;
         for (int c = 0; c < D; c++) d[c] = A.x[c * N + gi] - A.xs[c * N + gi];
         min_image<D>(H, d);
+        const float* u = warm ? A.warm_u + (g.off + A.perm[gi]) * D : nullptr;
         for (int c = 0; c < D; c++) {
-          double u = d[c] - sv[c] / n;
-          s2 += u * u;
+          double e = d[c] - sv[c] / n;
+          s2 += e * e;
+          double f = warm ? d[c] + dgam * (double)u[c] - sa[c] / n : e;
+          a2 += f * f;
         }
-        mx[0] = fmax(mx[0], s2);
+        mx[0] = fmax(mx[0], a2);
+        mx[1] = fmax(mx[1], s2);
       }
-      cluster_reduce(mx, 1, true);
+      cluster_reduce(mx, 2, true);
       if (rank == 0 && tid == 0 && A.rec) {
         double* rec = A.rec + ((int64_t)ri * A.rec_stride + step) * kRecFields;
         rec[0] = E;
@@ -930,6 +946,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         rec[2] = sqrt(mx[0]);
         rec[3] = (double)iters;
         rec[4] = (double)evals;
+        rec[5] = sqrt(mx[1]);
       }
       if (step == 0 && first_noaffine && want_snap && A.snap) {
         double* sp = A.snap + (int64_t)ri * A.snap_stride;

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -17,6 +18,7 @@
 #include "lists.cuh"
 #include "minimize.cuh"
 #include "misc.cuh"
+#include "warm.cuh"
 
 namespace aqs {
 static std::atomic<int64_t> g_launches{0};
@@ -99,6 +101,11 @@ struct aqs_system {
   double* d_rec = nullptr;
   int64_t rec_cap = 0;
   double* d_snap = nullptr;
+  // learned warm start buffers (allocated on first use)
+  __nv_bfloat16* d_feat = nullptr;
+  float* d_u = nullptr;
+  double* d_save = nullptr;
+  int* d_err = nullptr;
   // two-level stepping resources
   aqs_system* chains = nullptr;
   double* snap = nullptr;
@@ -421,6 +428,7 @@ MinArgs min_args(aqs_system* s, const aqs_fire_params* f) {
   a.snap = s->d_snap;
   a.snap_stride = (int64_t)s->dim * s->nmax;
   a.perm = s->perm;
+  a.warm_u = nullptr;
   return a;
 }
 
@@ -461,7 +469,7 @@ struct Job {
 };
 
 struct JobOut {
-  std::vector<double> rec;  // [R][nsteps_max][5]: E, tau, D_k, iterations, FP64 evaluations
+  std::vector<double> rec;  // [R][nsteps_max][kRecFields]
   int64_t stride = 0;
   std::vector<int64_t> rebuilds;
 };
@@ -470,7 +478,7 @@ aqs_status ensure_records(aqs_system* s, int64_t nsteps, bool snap) {
   if (nsteps > s->rec_cap) {
     dfree(s, s->d_rec);
     s->rec_cap = std::max<int64_t>(nsteps, 2 * s->rec_cap);
-    AQS_TRY(alloc_arr(s, &s->d_rec, (size_t)s->R * s->rec_cap * 5));
+    AQS_TRY(alloc_arr(s, &s->d_rec, (size_t)s->R * s->rec_cap * kRecFields));
   }
   if (snap && !s->d_snap) AQS_TRY(alloc_arr(s, &s->d_snap, (size_t)s->R * s->dim * s->nmax));
   return AQS_OK;
@@ -480,7 +488,7 @@ aqs_status ensure_records(aqs_system* s, int64_t nsteps, bool snap) {
 // persistent launches (one per cluster size and pass); between passes only
 // list rebuilds and budget yields are handled on the host.
 aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<Job>& jobs,
-                    JobOut* out) {
+                    JobOut* out, const float* warm_u = nullptr) {
   int64_t maxsteps = 0;
   bool snap = false;
   std::vector<int> todo;
@@ -520,6 +528,7 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
     CUDA_TRY(cudaMemcpyAsync(s->d_work, order_work.data(), sizeof(int) * order_work.size(),
                              cudaMemcpyHostToDevice, s->stream));
     MinArgs a = min_args(s, f);
+    a.warm_u = warm_u;
     const bool timing = g_timing.load() != 0;
     std::vector<RepState> before(s->st);
     if (timing) CUDA_TRY(cudaEventRecord(s->ev0, s->stream));
@@ -581,7 +590,7 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
   if (!todo.empty()) return fail(AQS_ERR_TIMEOUT, "minimiser jobs did not finish");
   if (out) {
     out->stride = s->rec_cap;
-    out->rec.assign((size_t)s->R * s->rec_cap * 5, 0.0);
+    out->rec.assign((size_t)s->R * s->rec_cap * kRecFields, 0.0);
     CUDA_TRY(cudaMemcpyAsync(out->rec.data(), s->d_rec, sizeof(double) * out->rec.size(),
                              cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -614,7 +623,7 @@ aqs_status minimize_impl(aqs_system* s, const aqs_fire_params* f, const std::vec
   for (int r = 0; r < s->R; r++) {
     if (!mask[r] || !res) continue;
     const RepState& t = s->st[r];
-    const double* rec = &out.rec[(size_t)r * out.stride * 5];
+    const double* rec = &out.rec[(size_t)r * out.stride * kRecFields];
     aqs_min_result& o = res[r];
     o.iters = t.status == AQS_OK ? (int64_t)rec[3] : t.iters;
     o.evals64 = t.status == AQS_OK ? (int64_t)rec[4] : t.evals64;
@@ -1050,7 +1059,7 @@ aqs_status aqs_run_sequential(aqs_system* s, const aqs_fire_params* f, double dg
   AQS_TRY(run_jobs(s, f, jobs, &out));
   for (int64_t k = 0; k < n_steps; k++)
     for (int r = 0; r < s->R; r++) {
-      const double* rec = &out.rec[((size_t)r * out.stride + k) * 5];
+      const double* rec = &out.rec[((size_t)r * out.stride + k) * kRecFields];
       size_t i = (size_t)k * s->R + r;
       if (energy) energy[i] = rec[0];
       if (tau) tau[i] = rec[1];
@@ -1107,11 +1116,11 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
     JobOut jo;
     AQS_TRY(run_jobs(c, f, jobs, &jo));
     for (int i = 0; i < P_eff; i++) {
-      const double* rec = &jo.rec[(size_t)i * jo.stride * 5];
+      const double* rec = &jo.rec[(size_t)i * jo.stride * kRecFields];
       out->fire_iters_total += (int64_t)rec[3];
       out->evals64_total += (int64_t)rec[4];
       for (int k = 0; k < Ki[i]; k++) {
-        const double* q = rec + (size_t)(k + 1) * 5;
+        const double* q = rec + (size_t)(k + 1) * kRecFields;
         cE[(size_t)i * K + k] = q[0];
         cT[(size_t)i * K + k] = q[1];
         cD[(size_t)i * K + k] = q[2];
@@ -1309,6 +1318,401 @@ double aqs_mean_neighbours(const aqs_system* s, int r) {
 
 int aqs_cluster_size(const aqs_system* s, int r) {
   return (s && r >= 0 && r < s->R) ? s->geom[r].C : 0;
+}
+
+}  // extern "C"
+
+// =====================================================================
+//                 learned warm start (C ABI, 2D workloads)
+// =====================================================================
+struct aqs_warm {
+  int dim = 2, n_types = 2;
+  cudaStream_t stream = nullptr;
+  MlpDev m{};
+  uint8_t* d_mask = nullptr;
+  float* d_grad = nullptr;
+  float* d_loss = nullptr;
+  int gblocks = 152;
+  int64_t adam_t = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+template <typename T>
+aqs_status walloc(aqs_warm* w, T** p, size_t count) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AQS_ERR_OOM, "warm start: device allocation failed");
+  }
+  w->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return AQS_OK;
+}
+
+uint16_t f2bf(float f) {  // round to nearest even
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+void param_mask(int dim, int n_types, std::vector<uint8_t>& mask) {
+  mask.assign(kNumParams, 1);
+  const int feat = kNb * dim + n_types;
+  for (int o = 0; o < kHid; o++)
+    for (int i = feat; i < kIn; i++) mask[o * kIn + i] = 0;  // W1 padding columns
+  const int w4 = kHid * kIn + 2 * kHid * kHid;
+  for (int o = dim; o < kOutPad; o++)
+    for (int i = 0; i < kHid; i++) mask[w4 + o * kHid + i] = 0;  // W4 padding rows
+  for (int o = dim; o < kOutPad; o++) mask[kNumWeights + 3 * kHid + o] = 0;  // b4 padding
+}
+
+aqs_status upload_params(aqs_warm* w, const std::vector<float>& p) {
+  std::vector<uint16_t> bf(kNumWeights);
+  for (int k = 0; k < kNumWeights; k++) bf[k] = f2bf(p[k]);
+  CUDA_TRY(cudaMemcpyAsync(w->m.master, p.data(), sizeof(float) * kNumParams,
+                           cudaMemcpyHostToDevice, w->stream));
+  CUDA_TRY(cudaMemcpyAsync(w->m.wbf, bf.data(), sizeof(uint16_t) * kNumWeights,
+                           cudaMemcpyHostToDevice, w->stream));
+  CUDA_TRY(cudaMemcpyAsync(w->m.b, p.data() + kNumWeights, sizeof(float) * kNumBiases,
+                           cudaMemcpyHostToDevice, w->stream));
+  CUDA_TRY(cudaMemsetAsync(w->m.m1, 0, sizeof(float) * kNumParams, w->stream));
+  CUDA_TRY(cudaMemsetAsync(w->m.m2, 0, sizeof(float) * kNumParams, w->stream));
+  CUDA_TRY(cudaStreamSynchronize(w->stream));
+  w->adam_t = 0;
+  return AQS_OK;
+}
+
+aqs_status ensure_warm_buffers(aqs_system* s) {
+  if (!s->d_feat) AQS_TRY(alloc_arr(s, &s->d_feat, (size_t)s->ntot * kIn));
+  if (!s->d_u) AQS_TRY(alloc_arr(s, &s->d_u, (size_t)s->ntot * s->dim));
+  if (!s->d_save) AQS_TRY(alloc_arr(s, &s->d_save, (size_t)s->ntot * s->dim));
+  if (!s->d_err) AQS_TRY(alloc_arr(s, &s->d_err, 1));
+  return AQS_OK;
+}
+
+// features of every replica, rows in caller order (replica r at rows off_r..)
+aqs_status features_all(aqs_system* s, __nv_bfloat16* bf, double* f64, int64_t row_base) {
+  if (s->dim != 2) return fail(AQS_ERR_UNSUPPORTED, "warm start features are built for 2D");
+  // the list build keeps cells current; make sure every replica's cell
+  // start table matches its atoms (rebuild is cheap and sorts the atoms)
+  AQS_TRY(rebuild_all(s));
+  CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+  for (int r = 0; r < s->R; r++) {
+    FeatArgs a;
+    a.geom = s->d_geom;
+    a.rep = r;
+    a.tilt = s->geom[r].H[1];
+    a.x = s->x;
+    a.type = s->type;
+    a.cell = s->cell;
+    a.cstart = s->cstart;
+    a.perm = s->perm;
+    a.inv = s->inv;
+    a.ntot = s->ntot;
+    a.nb = kNb;
+    a.n_types = s->nt;
+    a.half = 2;
+    double w[3];
+    cell_widths(s->dim, s->geom[r].H, w);
+    double cw = std::min(w[0] / s->geom[r].nc[0], w[1] / s->geom[r].nc[1]);
+    a.reach2 = (a.half * cw) * (a.half * cw);
+    a.bf = bf;
+    a.width = kIn;
+    a.f64 = f64;
+    a.width64 = kNb * s->dim + s->nt;
+    a.row0 = row_base + s->off[r];
+    a.err = s->d_err;
+    CUDA_TRY(launch_knn_features(s->dim, a, (int)s->n[r], s->stream));
+  }
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (err) return fail(AQS_ERR_BOX_TOO_SMALL, "neighbour-shell stencil too short for 32 neighbours");
+  return AQS_OK;
+}
+
+aqs_status save_positions(aqs_system* s) {
+  for (int r = 0; r < s->R; r++)
+    AQS_TRY(gather_user(s, r, s->d_save + (size_t)s->off[r] * s->dim));
+  return AQS_OK;
+}
+
+aqs_status restore_positions(aqs_system* s, const std::vector<uint8_t>& which,
+                             const std::vector<double>& tilt) {
+  for (int r = 0; r < s->R; r++) {
+    if (!which[r]) continue;
+    CUDA_TRY(launch_scatter_user(s->d_save + (size_t)s->off[r] * s->dim, s->x, s->ntot, s->off[r],
+                                 (int)s->n[r], s->perm, s->dim, s->stream));
+    s->geom[r].H[1] = tilt[r];
+  }
+  AQS_TRY(upload_geom(s));
+  sync_tilt_to_state(s);
+  AQS_TRY(upload_state(s));
+  return rebuild(s, which);
+}
+
+}  // namespace
+
+extern "C" {
+
+int aqs_warm_num_params(void) { return kNumParams; }
+
+aqs_status aqs_warm_create(int dim, int n_types, uint64_t seed, void* stream, aqs_warm** out) {
+  if (!out) return fail(AQS_ERR_INVALID_ARG, "null argument");
+  if (dim != 2) return fail(AQS_ERR_UNSUPPORTED, "the warm start network is built for 2D");
+  if (n_types < 1 || n_types > kIn - kNb * dim) return fail(AQS_ERR_INVALID_ARG, "bad n_types");
+  aqs_warm* w = new aqs_warm();
+  w->dim = dim;
+  w->n_types = n_types;
+  w->stream = (cudaStream_t)stream;
+  aqs_status st = AQS_OK;
+  __nv_bfloat16* wbf = nullptr;
+  if ((st = walloc(w, &wbf, kNumWeights)) != AQS_OK ||
+      (st = walloc(w, &w->m.b, kNumBiases)) != AQS_OK ||
+      (st = walloc(w, &w->m.master, kNumParams)) != AQS_OK ||
+      (st = walloc(w, &w->m.m1, kNumParams)) != AQS_OK ||
+      (st = walloc(w, &w->m.m2, kNumParams)) != AQS_OK ||
+      (st = walloc(w, &w->d_mask, kNumParams)) != AQS_OK ||
+      (st = walloc(w, &w->d_grad, kNumParams)) != AQS_OK ||
+      (st = walloc(w, &w->d_loss, w->gblocks)) != AQS_OK ||
+      (st = walloc(w, &w->m.gscratch, (size_t)w->gblocks * kNumParams)) != AQS_OK) {
+    aqs_warm_destroy(w);
+    return st;
+  }
+  w->m.wbf = wbf;
+  w->m.mask = w->d_mask;
+  // Glorot-uniform weights from a SplitMix64 stream, zero biases
+  std::vector<float> p(kNumParams, 0.0f);
+  std::vector<uint8_t> mask;
+  param_mask(dim, n_types, mask);
+  uint64_t z = seed * 0xD1B54A32D192ED03ull;
+  auto next = [&]() {
+    z += 0x9E3779B97F4A7C15ull;
+    uint64_t t = z;
+    t = (t ^ (t >> 30)) * 0xBF58476D1CE4E5B9ull;
+    t = (t ^ (t >> 27)) * 0x94D049BB133111EBull;
+    t ^= t >> 31;
+    return (double)(t >> 11) * (1.0 / 9007199254740992.0);
+  };
+  const int fan_in[4] = {kNb * dim + n_types, kHid, kHid, kHid};
+  const int fan_out[4] = {kHid, kHid, kHid, dim};
+  const int nin[4] = {kIn, kHid, kHid, kHid}, nout[4] = {kHid, kHid, kHid, kOutPad};
+  int off = 0;
+  for (int l = 0; l < 4; l++) {
+    const double lim = std::sqrt(6.0 / (fan_in[l] + fan_out[l]));
+    for (int k = 0; k < nin[l] * nout[l]; k++) {
+      double u = next();
+      p[off + k] = mask[off + k] ? (float)((2.0 * u - 1.0) * lim) : 0.0f;
+    }
+    off += nin[l] * nout[l];
+  }
+  if (cudaMemcpy(w->d_mask, mask.data(), kNumParams, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (st = upload_params(w, p)) != AQS_OK) {
+    aqs_warm_destroy(w);
+    return st != AQS_OK ? st : fail(AQS_ERR_CUDA, "warm start upload failed");
+  }
+  *out = w;
+  return AQS_OK;
+}
+
+void aqs_warm_destroy(aqs_warm* w) {
+  if (!w) return;
+  cudaStreamSynchronize(w->stream);
+  for (void* p : w->allocs) cudaFree(p);
+  delete w;
+}
+
+aqs_status aqs_warm_get_params(const aqs_warm* w, float* host) {
+  if (!w || !host) return fail(AQS_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(cudaMemcpyAsync(host, w->m.master, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost,
+                           w->stream));
+  CUDA_TRY(cudaStreamSynchronize(w->stream));
+  return AQS_OK;
+}
+
+aqs_status aqs_warm_set_params(aqs_warm* w, const float* host) {
+  if (!w || !host) return fail(AQS_ERR_INVALID_ARG, "null argument");
+  std::vector<float> p(host, host + kNumParams);
+  std::vector<uint8_t> mask;
+  param_mask(w->dim, w->n_types, mask);
+  for (int k = 0; k < kNumParams; k++)
+    if (!mask[k]) p[k] = 0.0f;
+  return upload_params(w, p);
+}
+
+aqs_status aqs_warm_features(aqs_system* s, int replica, void* feat_bf16, double* feat_f64) {
+  if (!s || !feat_bf16) return fail(AQS_ERR_INVALID_ARG, "null argument");
+  if (replica < -1 || replica >= s->R) return fail(AQS_ERR_INVALID_ARG, "bad replica");
+  AQS_TRY(ensure_warm_buffers(s));
+  // rows of all replicas are written; a single replica's rows start at 0
+  const int64_t base = replica >= 0 ? -s->off[replica] : 0;
+  if (replica >= 0) {
+    // only the chosen replica: write into the caller's buffer, others to scratch
+    AQS_TRY(features_all(s, s->d_feat, nullptr, 0));
+    (void)base;
+    if (s->dim != 2) return AQS_ERR_UNSUPPORTED;
+    FeatArgs a;  // recompute the chosen replica straight into the caller's rows
+    a.geom = s->d_geom;
+    a.rep = replica;
+    a.tilt = s->geom[replica].H[1];
+    a.x = s->x;
+    a.type = s->type;
+    a.cell = s->cell;
+    a.cstart = s->cstart;
+    a.perm = s->perm;
+    a.inv = s->inv;
+    a.ntot = s->ntot;
+    a.nb = kNb;
+    a.n_types = s->nt;
+    a.half = 2;
+    double w[3];
+    cell_widths(s->dim, s->geom[replica].H, w);
+    double cw = std::min(w[0] / s->geom[replica].nc[0], w[1] / s->geom[replica].nc[1]);
+    a.reach2 = (a.half * cw) * (a.half * cw);
+    a.bf = static_cast<__nv_bfloat16*>(feat_bf16);
+    a.width = kIn;
+    a.f64 = feat_f64;
+    a.width64 = kNb * s->dim + s->nt;
+    a.row0 = 0;
+    a.err = s->d_err;
+    CUDA_TRY(launch_knn_features(s->dim, a, (int)s->n[replica], s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return AQS_OK;
+  }
+  return features_all(s, static_cast<__nv_bfloat16*>(feat_bf16), feat_f64, 0);
+}
+
+aqs_status aqs_warm_predict(aqs_warm* w, const void* feat_bf16, int64_t rows, float* out) {
+  if (!w || !feat_bf16 || !out || rows < 0) return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  if (rows == 0) return AQS_OK;
+  CUDA_TRY(launch_mlp_forward(w->m, static_cast<const __nv_bfloat16*>(feat_bf16), rows, out, w->dim,
+                              w->stream));
+  return AQS_OK;
+}
+
+aqs_status aqs_warm_loss_grad(aqs_warm* w, const void* feat_bf16, const float* target,
+                              int64_t rows, float* grad_host, double* loss) {
+  if (!w || !feat_bf16 || !target || rows <= 0) return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  const int blocks = (int)std::min<int64_t>(w->gblocks, (rows + 31) / 32);
+  CUDA_TRY(launch_mlp_grad(w->m, static_cast<const __nv_bfloat16*>(feat_bf16), target, rows, w->dim,
+                           blocks, w->d_grad, w->d_loss, w->stream));
+  std::vector<float> lp(blocks);
+  CUDA_TRY(cudaMemcpyAsync(lp.data(), w->d_loss, sizeof(float) * blocks, cudaMemcpyDeviceToHost,
+                           w->stream));
+  if (grad_host)
+    CUDA_TRY(cudaMemcpyAsync(grad_host, w->d_grad, sizeof(float) * kNumParams,
+                             cudaMemcpyDeviceToHost, w->stream));
+  CUDA_TRY(cudaStreamSynchronize(w->stream));
+  double l = 0.0;
+  for (float v : lp) l += v;
+  if (loss) *loss = l;
+  return AQS_OK;
+}
+
+aqs_status aqs_warm_train_step(aqs_warm* w, const void* feat_bf16, const float* target,
+                               int64_t rows, double lr, double weight_decay, double* loss) {
+  AQS_TRY(aqs_warm_loss_grad(w, feat_bf16, target, rows, nullptr, loss));
+  w->adam_t++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float bc1 = 1.0f - std::pow(b1, (float)w->adam_t), bc2 = 1.0f - std::pow(b2, (float)w->adam_t);
+  CUDA_TRY(launch_mlp_adamw(w->m, w->d_grad, (float)lr, b1, b2, 1e-8f, (float)weight_decay, bc1, bc2,
+                            w->stream));
+  return AQS_OK;
+}
+
+aqs_status aqs_warm_collect(aqs_system* s, const aqs_fire_params* f, double dgamma, int64_t n_steps,
+                            void* feat_out, float* target_out) {
+  if (!s || !f || !feat_out || !target_out || n_steps < 0)
+    return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  AQS_TRY(ensure_warm_buffers(s));
+  __nv_bfloat16* fo = static_cast<__nv_bfloat16*>(feat_out);
+  for (int64_t k = 0; k < n_steps; k++) {
+    AQS_TRY(features_all(s, fo + (size_t)k * s->ntot * kIn, nullptr, 0));
+    std::vector<Job> jobs(s->R);
+    for (int r = 0; r < s->R; r++) {
+      jobs[r].nsteps = 1;
+      jobs[r].dgamma = dgamma;
+    }
+    AQS_TRY(run_jobs(s, f, jobs, nullptr));
+    for (int r = 0; r < s->R; r++)
+      CUDA_TRY(launch_step_target(s->dim, s->x, s->xs, s->ntot, s->off[r], (int)s->n[r], s->perm,
+                                  reinterpret_cast<const double*>(
+                                      reinterpret_cast<const char*>(s->d_geom + r) +
+                                      offsetof(RepGeom, H)),
+                                  1.0 / dgamma,
+                                  target_out + ((size_t)k * s->ntot + s->off[r]) * s->dim,
+                                  s->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return AQS_OK;
+}
+
+aqs_status aqs_run_sequential_warm(aqs_system* s, const aqs_fire_params* f, aqs_warm* w,
+                                   double dgamma, int64_t n_steps, double gate, double* energy,
+                                   double* tau, int64_t* fire_iters, double* nonaffine,
+                                   uint8_t* used_warm) {
+  if (!s || !f || !w || n_steps < 0) return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  if (w->dim != s->dim || w->n_types != s->nt)
+    return fail(AQS_ERR_INVALID_ARG, "network and system differ in dimension or species");
+  if (!(gate > 0.0)) gate = 1e-2;
+  AQS_TRY(ensure_warm_buffers(s));
+  for (int64_t k = 0; k < n_steps; k++) {
+    // prediction for the step from the current minima
+    AQS_TRY(features_all(s, s->d_feat, nullptr, 0));
+    CUDA_TRY(launch_mlp_forward(w->m, s->d_feat, s->ntot, s->d_u, s->dim, s->stream));
+    AQS_TRY(save_positions(s));
+    std::vector<double> tilt(s->R);
+    for (int r = 0; r < s->R; r++) tilt[r] = s->geom[r].H[1];
+    std::vector<Job> jobs(s->R);
+    for (int r = 0; r < s->R; r++) {
+      jobs[r].nsteps = 1;
+      jobs[r].dgamma = dgamma;
+    }
+    JobOut jo;
+    AQS_TRY(run_jobs(s, f, jobs, &jo, s->d_u));
+    // gate: keep the learned start only where the step stayed elastic, i.e.
+    // the minimum lies within `gate` of both the learned and the affine start
+    std::vector<uint8_t> redo(s->R, 0);
+    bool any = false;
+    for (int r = 0; r < s->R; r++) {
+      const double* q = &jo.rec[(size_t)r * jo.stride * kRecFields];
+      if (!(q[2] < gate && q[5] < gate)) {
+        redo[r] = 1;
+        any = true;
+      }
+    }
+    std::vector<double> rec_keep = jo.rec;
+    if (any) {
+      AQS_TRY(restore_positions(s, redo, tilt));
+      std::vector<Job> plain(s->R);
+      for (int r = 0; r < s->R; r++)
+        if (redo[r]) {
+          plain[r].nsteps = 1;
+          plain[r].dgamma = dgamma;
+        }
+      JobOut jp;
+      AQS_TRY(run_jobs(s, f, plain, &jp));
+      for (int r = 0; r < s->R; r++)
+        if (redo[r])
+          for (int c = 0; c < kRecFields; c++)
+            rec_keep[(size_t)r * jo.stride * kRecFields + c] =
+                jp.rec[(size_t)r * jp.stride * kRecFields + c] +
+                (c == 3 || c == 4 ? jo.rec[(size_t)r * jo.stride * kRecFields + c] : 0.0);
+    }
+    for (int r = 0; r < s->R; r++) {
+      const double* q = &rec_keep[(size_t)r * jo.stride * kRecFields];
+      size_t i = (size_t)k * s->R + r;
+      if (energy) energy[i] = q[0];
+      if (tau) tau[i] = q[1];
+      if (fire_iters) fire_iters[i] = (int64_t)q[3];
+      if (nonaffine) nonaffine[i] = q[2];
+      if (used_warm) used_warm[i] = redo[r] ? 0 : 1;
+    }
+  }
+  return AQS_OK;
 }
 
 }  // extern "C"
