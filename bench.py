@@ -181,6 +181,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-iters", type=int, default=40)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--baseline-steps", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -297,6 +299,26 @@ def main():
                 "pair_visits_fp32": st["pairs32"], "pair_visits_fp64": st["pairs64"],
                 "peak_note": "FP32 peak derived from 152 SMs x 128 lanes x 2 x 2.07 GHz"}
 
+    # ---------------- plain FP64 sequential GPU AQS on the same glass (the
+    # denominator of the speed-up target): same kernels in FP64 mode, one
+    # replica, no batching, no warm start, a bounded number of steps
+    base = None
+    if rank == 0 and not args.no_baseline:
+        xb_ = s.positions()
+        b = A.System(xb_, t, s.box()[None], [N_ATOMS], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
+                     precision=A.AQS_FP64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ob = b.run_sequential(DGAMMA, args.baseline_steps)
+        e1.record()
+        e1.synchronize()
+        bsec = e0.elapsed_time(e1) / 1e3
+        base = {"value": args.baseline_steps / bsec, "unit": UNIT, "steps": args.baseline_steps,
+                "fire_iters_per_step": float(ob["iters"].mean()),
+                "cluster_size": b.cluster_size(), "speedup_of_value": value / (args.baseline_steps / bsec)}
+        b.close()
+
     # ---------------- CPU baseline (oracle, rank 0, N = 1 only)
     cpu = None
     mean_iters = float(np.mean(iters)) if iters else float("nan")
@@ -317,6 +339,7 @@ def main():
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(gpu_launches), "clocks": clocks, "roofline": roofline,
                 "cpu_baseline": cpu,
+                "fp64_sequential_gpu_baseline": base,
                 "detail": {"accepted_steps": int(total_steps), "rejections": rej,
                            "wall_s": wall, "fire_iters_per_step": mean_iters,
                            "fp32_evals": st["evals32"], "fp64_evals": st["evals64"],
