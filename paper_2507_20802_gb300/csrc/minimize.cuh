@@ -15,9 +15,17 @@ struct MinArgs {
   double* xs;       // [D][ntot] positions at the start of the minimisation
   double* xb;       // [D][ntot] positions at the last list build (affinely mapped)
   const int32_t* type;
-  const int32_t* cell;
-  const uint32_t* nb;
-  const int32_t* nnb;
+  int32_t* cell;
+  uint32_t* nb;
+  int32_t* nnb;
+  // in-kernel Verlet rebuild (without re-sorting the atoms): scratch per cell
+  // (count, cstart at the replica's cell_off) and per atom (cellatoms)
+  int32_t* count;
+  int32_t* cstart;
+  int32_t* cellatoms;
+  int cap;                // list capacity per atom
+  int inkernel_rebuild;   // 1: rebuild lists inside the kernel when the skin trips
+  float rl2f[AQS_MAX_TYPES * AQS_MAX_TYPES];
   const PairCoef* coef;
   int64_t ntot;
   int nt;

@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   const bool want_snap = st->want_snap != 0;
   const double dgam = st->dgamma;
   int phase = st->phase;  // 0: the next step has not started, 1: FIRE in progress
-  const double tilt_b = st->tilt_b;
+  double tilt_b = st->tilt_b;  // changes when the kernel rebuilds the list
   // FIRE scalars (meaningful in thread 0 only)
   double dt = st->dt, alpha = st->alpha;
   float dtf = (float)dt, alphaf = (float)alpha;  // mixed mode keeps these in FP32
@@ -355,6 +355,183 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
     cl.sync();  // every CTA has read the partials before they are reused
     for (int m = 0; m < nv; m++) v[m] = shv[m];
   };
+
+  // ---- in-kernel Verlet rebuild (the atoms keep their CTA and slot) ----
+  // Called by every thread of every CTA of the cluster with x materialised.
+  // Returns false (uniformly) when the host must take over: the cell grid no
+  // longer covers rc + skin at the current tilt, or a list would overflow.
+  auto rebuild_lists = [&]() -> bool {
+    // cell grid still wide enough for the 3^d stencil at the current tilt?
+    {
+      const double t = H[1] / H[D + 1];
+      double w = (H[0] / sqrt(1.0 + t * t)) / g.nc[0];
+      w = fmin(w, H[D + 1] / g.nc[1]);
+      if (D == 3) w = fmin(w, H[8] / g.nc[2]);
+      if (!(w >= A.rlist)) return false;
+    }
+    const int32_t coff = g.cell_off;
+    const int ncell = g.ncell;
+    const int64_t aoff = g.off;
+    // 1. wrap own atoms into the cell (by whole lattice vectors, the same
+    //    shift applied to the step's start positions), new cell keys
+    for (int c = rank * nthr + tid; c <= ncell; c += C * nthr) A.count[coff + c] = 0;
+#pragma unroll
+    for (int k = 0; k < APT; k++) {
+      int li = tid + k * nthr;
+      if (li >= cnt) continue;
+      int64_t gi = base + li;
+      double xv[3], sv[3];
+      for (int c = 0; c < D; c++) xv[c] = A.x[c * N + gi];
+      for (int c = D - 1; c >= 0; c--) {
+        double tt = xv[c];
+        for (int kk = c + 1; kk < D; kk++) tt -= H[c * D + kk] * sv[kk];
+        sv[c] = tt / H[c * D + c];
+      }
+      int key = 0, mul = 1;
+      for (int c = 0; c < D; c++) {
+        double nf = floor(sv[c]);
+        if (nf != 0.0)
+          for (int a = 0; a <= c; a++) {
+            A.x[a * N + gi] -= nf * H[a * D + c];
+            A.xs[a * N + gi] -= nf * H[a * D + c];
+          }
+        int ic = (int)floor((sv[c] - nf) * g.nc[c]);
+        ic = ic < 0 ? 0 : (ic >= g.nc[c] ? g.nc[c] - 1 : ic);
+        key += ic * mul;
+        mul *= g.nc[c];
+      }
+      A.cell[gi] = key;
+    }
+    cl.sync();
+    // 2. histogram
+#pragma unroll
+    for (int k = 0; k < APT; k++) {
+      int li = tid + k * nthr;
+      if (li < cnt) atomicAdd(&A.count[coff + A.cell[base + li]], 1);
+    }
+    cl.sync();
+    // 3. exclusive scan (rank 0), counts become scatter cursors
+    if (rank == 0) {
+      int* swsum = reinterpret_cast<int*>(wred);  // [32] warp sums, [32] carry
+      int& scarry = swsum[32];
+      if (tid == 0) scarry = 0;
+      __syncthreads();
+      for (int b0 = 0; b0 < ncell; b0 += nthr) {
+        const int c = b0 + tid;
+        const int v = c < ncell ? A.count[coff + c] : 0;
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+          int tt = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += tt;
+        }
+        if (lane == 31) swsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+          int ws = lane < nwarp ? swsum[lane] : 0;
+          for (int o = 1; o < 32; o <<= 1) {
+            int tt = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= o) ws += tt;
+          }
+          if (lane < nwarp) swsum[lane] = ws;
+        }
+        __syncthreads();
+        if (c < ncell) {
+          A.cstart[coff + c] = scarry + (warp > 0 ? swsum[warp - 1] : 0) + incl - v;
+          A.count[coff + c] = 0;
+        }
+        __syncthreads();
+        if (tid == 0) scarry += swsum[nwarp - 1];
+        __syncthreads();
+      }
+      if (tid == 0) A.cstart[coff + ncell] = scarry;
+    }
+    cl.sync();
+    // 4. scatter replica-local indices into the cells
+#pragma unroll
+    for (int k = 0; k < APT; k++) {
+      int li = tid + k * nthr;
+      if (li >= cnt) continue;
+      const int key = A.cell[base + li];
+      const int p = A.cstart[coff + key] + atomicAdd(&A.count[coff + key], 1);
+      A.cellatoms[aoff + p] = lo + li;
+    }
+    cl.sync();
+    // 5. deterministic order inside each cell
+    for (int c = rank * nthr + tid; c < ncell; c += C * nthr) {
+      const int b = A.cstart[coff + c], e = A.cstart[coff + c + 1];
+      for (int i = b + 1; i < e; i++) {
+        const int v = A.cellatoms[aoff + i];
+        int j = i - 1;
+        while (j >= b && A.cellatoms[aoff + j] > v) {
+          A.cellatoms[aoff + j + 1] = A.cellatoms[aoff + j];
+          j--;
+        }
+        A.cellatoms[aoff + j + 1] = v;
+      }
+    }
+    cl.sync();
+    // 6. Verlet rows of the own atoms (same test as the host-side build),
+    //    written to the global list and, when staged, to shared memory
+    if (MEM == 2 && tid == 0) need = 0u;
+    __syncthreads();
+    double over = 0.0;
+    const int ncode = D == 2 ? 9 : 27;
+#pragma unroll
+    for (int k = 0; k < APT; k++) {
+      int li = tid + k * nthr;
+      if (li >= cnt) continue;
+      const int64_t gi = base + li;
+      const int il = lo + li;
+      const int ci = A.cell[gi];
+      int cc[3] = {ci % g.nc[0], (ci / g.nc[0]) % g.nc[1], D == 3 ? ci / (g.nc[0] * g.nc[1]) : 0};
+      double oi[3];
+      cell_origin<D>(H, g.nc, ci, oi);
+      float qi[3];
+      for (int c = 0; c < D; c++) qi[c] = (float)(A.x[c * N + gi] - oi[c]);
+      const int ti = ty[k];
+      int m = 0;
+      unsigned own = 0u;
+      for (int code = 0; code < ncode; code++) {
+        const int dx = code % 3 - 1, dy = (code / 3) % 3 - 1, dz = code / 9 - 1;
+        const int nx = (cc[0] + dx + g.nc[0]) % g.nc[0];
+        const int ny = (cc[1] + dy + g.nc[1]) % g.nc[1];
+        const int nz = D == 3 ? (cc[2] + dz + g.nc[2]) % g.nc[2] : 0;
+        const int cj = nx + g.nc[0] * (ny + g.nc[1] * nz);
+        double oj[3];
+        cell_origin<D>(H, g.nc, cj, oj);
+        const float* of = off32 + 3 * code;
+        const int b = A.cstart[g.cell_off + cj], e = A.cstart[g.cell_off + cj + 1];
+        for (int p = b; p < e; p++) {
+          const int jl = A.cellatoms[g.off + p];
+          if (jl == il) continue;
+          const int64_t gj = g.off + jl;
+          float s2 = 0.0f;
+          for (int c = 0; c < D; c++) {
+            float d = ((float)(A.x[c * N + gj] - oj[c]) - qi[c]) + of[c];
+            s2 = fmaf(d, d, s2);
+          }
+          const int tj = A.type[gj];
+          if (s2 < A.rl2f[ti * A.nt + tj]) {
+            if (m < A.cap) {
+              const uint32_t ent = encode_nb(jl % npc, jl / npc, code, tj);
+              A.nb[g.nb_off + (int64_t)m * n + il] = ent;
+              if (LSM && m < A.cap) lst[m * lstride + li] = ent;
+              own |= 1u << (jl / npc);
+            }
+            m++;
+          }
+        }
+      }
+      A.nnb[gi] = m < A.cap ? m : A.cap;
+      if (m > A.cap) over = 1.0;
+      if (MEM == 2 && own) atomicOr(&need, own);
+      for (int c = 0; c < D; c++) A.xb[c * N + gi] = A.x[c * N + gi];
+    }
+    double ov[1] = {over};
+    cluster_reduce(ov, 1, true);  // also orders the list writes before their use
+    return ov[0] == 0.0;
+  };
+
 
   for (;;) {
     if (step >= nsteps) {
@@ -896,6 +1073,15 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         }
       }
     }
+    if (status == kStatusRebuild && A.inkernel_rebuild) {
+      // rebuild the lists here and resume the same FIRE state
+      if (rebuild_lists()) {
+        tilt_b = H[1];
+        wmaxf = 0.0f;
+        status = kStatusRunning;
+        continue;  // republishes FP64 positions; the next evaluation is FP64
+      }
+    }
     if (status != AQS_OK) break;  // rebuild, budget or error: the next launch resumes
     // ---- step converged: non-affine displacement D_k, records, snapshot ----
     {
@@ -996,6 +1182,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
     st->step = step;
     st->phase = phase;
     st->tilt = H[1];
+    st->tilt_b = tilt_b;
     if (status == AQS_OK) {
       st->E = E;
       st->tau = W;

@@ -429,6 +429,12 @@ MinArgs min_args(aqs_system* s, const aqs_fire_params* f) {
   a.snap_stride = (int64_t)s->dim * s->nmax;
   a.perm = s->perm;
   a.warm_u = nullptr;
+  a.count = s->count;
+  a.cstart = s->cstart;
+  a.cellatoms = s->itmp;  // host rebuilds use it only between launches
+  a.cap = s->cap;
+  a.inkernel_rebuild = 1;
+  for (int k = 0; k < AQS_MAX_TYPES * AQS_MAX_TYPES; k++) a.rl2f[k] = s->rl2f[k];
   return a;
 }
 
