@@ -52,7 +52,7 @@ FLOP64_PER_PAIR = 32
 # mean FIRE iterations per accepted fine step of this workload, used only to
 # express the reference arm's oracle sample in steps/s (measured by this
 # benchmark's own arm; see profiles/bench_cfg1_n4096.md)
-ITERS_PER_STEP_REF = 20000
+ITERS_PER_STEP_REF = 21000
 
 CONFIG = {"workload": "2D binary LJ glass (65:35, rho=1.2), N=4096, Algorithm 1 with P=16 "
                       "chains of K=10 fine steps, dgamma=1e-4, FIRE to |F|max<1e-10, mixed "
