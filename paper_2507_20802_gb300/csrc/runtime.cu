@@ -73,6 +73,9 @@ struct aqs_system {
   std::vector<int64_t> nnb_sum;
   int64_t* d_nnbsum = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // launches of different cluster sizes run concurrently on these streams
+  cudaStream_t aux[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t aux_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   PairCoef coef[AQS_MAX_TYPES * AQS_MAX_TYPES];
   float rl2f[AQS_MAX_TYPES * AQS_MAX_TYPES];
   int total_cells = 0, cells_cap = 0;
@@ -538,6 +541,16 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
     const bool timing = g_timing.load() != 0;
     std::vector<RepState> before(s->st);
     if (timing) CUDA_TRY(cudaEventRecord(s->ev0, s->stream));
+    const bool multi = groups.size() > 1;
+    if (multi) {
+      if (!s->aux[0])
+        for (int k = 0; k < 4; k++) {
+          CUDA_TRY(cudaStreamCreateWithFlags(&s->aux[k], cudaStreamNonBlocking));
+          CUDA_TRY(cudaEventCreateWithFlags(&s->aux_ev[k], cudaEventDisableTiming));
+        }
+      if (!s->aux_ev[4]) CUDA_TRY(cudaEventCreateWithFlags(&s->aux_ev[4], cudaEventDisableTiming));
+      CUDA_TRY(cudaEventRecord(s->aux_ev[4], s->stream));
+    }
     for (size_t gi = 0; gi < groups.size(); gi++) {
       int C = Cs[gi];
       int npc = 0, nrep = 0;
@@ -546,8 +559,16 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
         nrep = std::max(nrep, s->geom[order_work[groups[gi].first + k]].n);
       }
       a.work = s->d_work + groups[gi].first;
+      cudaStream_t st = s->stream;
+      if (multi) {
+        st = s->aux[gi % 4];
+        CUDA_TRY(cudaStreamWaitEvent(st, s->aux_ev[4], 0));
+      }
       CUDA_TRY(launch_minimize(s->dim, s->prec == AQS_MIXED, a, groups[gi].second, C, npc, nrep,
-                               s->cap, s->stream));
+                               s->cap, st));
+      if (multi) CUDA_TRY(cudaEventRecord(s->aux_ev[gi % 4], st));
+      if (multi && (gi % 4 == 3 || gi + 1 == groups.size()))
+        for (size_t k = 0; k <= gi % 4; k++) CUDA_TRY(cudaStreamWaitEvent(s->stream, s->aux_ev[k], 0));
     }
     if (timing) CUDA_TRY(cudaEventRecord(s->ev1, s->stream));
     AQS_TRY(download_state(s));
@@ -814,6 +835,13 @@ void destroy(aqs_system* s) {
   cudaStreamSynchronize(s->stream);
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
+  for (int k = 0; k < 4; k++)
+    if (s->aux[k]) {
+      cudaStreamSynchronize(s->aux[k]);
+      cudaStreamDestroy(s->aux[k]);
+    }
+  for (int k = 0; k < 5; k++)
+    if (s->aux_ev[k]) cudaEventDestroy(s->aux_ev[k]);
   for (auto& a : s->allocs) {
     if (s->ufree) s->ufree(a.p, s->actx);
     else cudaFree(a.p);

@@ -250,3 +250,46 @@ def test_quench_from_random_start_converges(A, syn, prec):
     assert np.sqrt((F * F).sum(1)).max() < 1e-10
     assert E == pytest.approx(r["E"], rel=1e-12)
     assert E / len(x) < -2.5  # a bound glass, not an exploded configuration
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_3d_trajectory_matches_golden(A, syn, prec):
+    """3D glass (80:20, N = 2048, the oracle's quench), three AQS steps of
+    dgamma = 5e-5 against the stored oracle run."""
+    g = load_golden("glass_3d_n2048_s0.npz")
+    gold = load_golden("aqs_3d_n2048_s0.npz")
+    P = A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED
+    s = make_system(A, syn, g["x"], g["types"], g["H"], P)
+    out = s.run_sequential(float(gold["dgamma"]), int(gold["n_steps"]))
+    rel = 1e-9 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(out["E"][:, 0], gold["E"], rtol=rel)
+    np.testing.assert_allclose(out["tau"][:, 0], gold["tau"], rtol=1e-6, atol=1e-7)
+    assert mi_disp(s.positions(), gold["x"], gold["H"]) < 1e-6
+    np.testing.assert_allclose(out["D"][:, 0], gold["D"], rtol=1e-3)
+
+
+def test_uneven_batch_reproduces_single_glass_trajectory(A, syn, glass256):
+    """Replicas of different sizes in one batched run (different cluster sizes,
+    concurrent launches): replica 0 is the stored N = 256 glass and must follow
+    the oracle's 200-step trajectory; the others must converge every step."""
+    gold = load_golden("aqs_2d_n256_s0.npz")
+    sizes = [256, 1500, 700, 3000, 1024]
+    xs, ts, Hs = [glass256["x"]], [glass256["types"]], [glass256["H"]]
+    for k, n in enumerate(sizes[1:]):
+        x, t, H = syn.random_glass_start(n, 2, seed=1000 + k)
+        q = make_system(A, syn, x, t, H, A.AQS_MIXED)
+        q.minimize(A.fire_params(max_iter=500000))
+        xs.append(q.positions())
+        ts.append(t)
+        Hs.append(q.box())
+        q.close()
+    s = A.System(np.concatenate(xs), np.concatenate(ts), np.stack(Hs), sizes, syn.LJ_SIGMA,
+                 syn.LJ_EPS, precision=A.AQS_MIXED)
+    assert len({s.cluster_size(r) for r in range(len(sizes))}) >= 2
+    out = s.run_sequential(float(gold["dgamma"]), int(gold["n_steps"]))
+    np.testing.assert_allclose(out["E"][:, 0], gold["E"], rtol=1e-6)
+    assert np.array_equal(out["D"][:, 0] > EV_THR, gold["D"] > EV_THR)
+    assert mi_disp(s.positions(0), gold["x"], gold["H"]) < 1e-6
+    for r in range(1, len(sizes)):
+        _, F, _ = s.energy_forces(r)
+        assert np.sqrt((F * F).sum(1)).max() < 1e-10
