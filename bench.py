@@ -126,6 +126,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def combine_ranks(secs, units, device):
+    """Whole-job figures over the ranks (weak scaling, one glass per rank):
+    the sum of the units every rank processed and the slowest rank's time.
+    Returns (units, seconds); a single process returns its own figures."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(units), float(secs)
+    tt = torch.tensor([float(secs), float(units)], device=device, dtype=torch.float64)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(tt[1]), float(mx[0])
+
+
 def oracle_iteration_rate(n_iters: int, seed: int = 0):
     """FIRE iterations per second of the FP64 oracle on this workload's size
     (all-pairs forces dominate, so the rate does not depend on the
@@ -172,6 +187,124 @@ def run_reference(args):
     return 0
 
 
+def _line(metric, value, unit, args, ms, config, extra):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config}
+    d.update(extra)
+    print(json.dumps(d), flush=True)
+
+
+def run_batch64(args):
+    """64 independent 2D glasses of log-uniform size in [1024, 16384] (sizes
+    from stream seed 2, glass r from seed 1000 + r), plain AQS dgamma = 5e-5,
+    all in one batched system (per-replica convergence, concurrent launches
+    for the different cluster sizes).  value = glass-steps / s."""
+    import torch
+    from paper_2507_20802_gb300 import aqs as A, synthetic as syn
+    torch.cuda.set_device(0)
+    sizes = syn.log_uniform_sizes(64, 1024, 16384, seed=2)
+    xs, ts, Hs = [], [], []
+    for r, n in enumerate(sizes):
+        x, t, H = syn.random_glass_start(int(n), 2, seed=1000 + r)
+        xs.append(x); ts.append(t); Hs.append(H)
+    s = A.System(np.concatenate(xs), np.concatenate(ts), np.stack(Hs), sizes, syn.LJ_SIGMA,
+                 syn.LJ_EPS, syn.RC_FACTOR, precision=A.AQS_MIXED)
+    res = s.minimize(A.fire_params(max_iter=2_000_000))
+    quench = int(max(q["iters"] for q in res))
+    for _ in range(args.warmup):
+        s.run_sequential(5e-5, 1)
+    A.aqs_reset_kernel_stats()
+    A.aqs_set_kernel_timing(True)
+    l0 = A.aqs_launch_count()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record()
+        out = s.run_sequential(5e-5, args.steps)
+        e1.record()
+        e1.synchronize()
+    st = A.aqs_get_kernel_stats()
+    A.aqs_set_kernel_timing(False)
+    secs = e0.elapsed_time(e1) / 1e3
+    value = 64 * args.steps / secs
+    kern_s = st["kernel_ms"] / 1e3
+    achieved = st["pairs32"] * FLOP32_PER_PAIR / kern_s / 1e12 if kern_s else 0.0
+    config = {"workload": "64 independent 2D binary LJ glasses, N log-uniform in [1024, 16384] "
+                          "(sum %d), plain AQS dgamma=5e-5, batched mixed precision" % int(sizes.sum()),
+              "n_glasses": 64, "atoms_total": int(sizes.sum()), "dgamma": 5e-5,
+              "l2": "working set on chip / L2; not flushed"}
+    _line("converged AQS glass-steps/s (64 glasses batched)", value, "glass-steps/s", args,
+          1e3 * secs / max(1, args.steps), config,
+          {"gpu_launches": A.aqs_launch_count() - l0, "clocks": clk.summary(),
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None},
+           "detail": {"fire_iters_per_step_mean": float(out["iters"].mean()),
+                      "fire_iters_per_step_max": int(out["iters"].max()), "quench_iters_max": quench,
+                      "cluster_sizes": sorted({s.cluster_size(r) for r in range(64)})}})
+
+
+def run_glass3d(args):
+    """3D binary LJ glass (80:20, N = 65536, density 1.2): the 32 level-I
+    predictions of Algorithm 1 (shear i * 20 * 5e-5 of the quenched glass) as
+    32 replicas, minimised together for a bounded number of FIRE iterations.
+    value = FIRE iterations / s summed over the replicas; the roofline reports
+    the force kernel's streamed list and position bytes against HBM."""
+    import torch
+    from paper_2507_20802_gb300 import aqs as A, synthetic as syn
+    torch.cuda.set_device(0)
+    n, P, K, dg = 65536, 32, 20, 5e-5
+    x, t, H = syn.random_glass_start(n, 3, seed=0)
+    s = A.System(x, t, H[None], [n], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
+                 precision=A.AQS_MIXED)
+    q = s.minimize(A.fire_params(max_iter=args.quench_iters), check_status=False)[0]
+    xq, Hq = s.positions(), s.box()
+    s.close()
+    b = A.System(np.tile(xq, (P, 1)), np.tile(t, P), np.tile(Hq[None], (P, 1, 1)), [n] * P,
+                 syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR, precision=A.AQS_MIXED)
+    b.shear(np.arange(P) * K * dg)
+    nb = b.mean_neighbours(0)
+    budget = args.iters3d
+    b.minimize(A.fire_params(max_iter=50), check_status=False)  # warm-up
+    A.aqs_reset_kernel_stats()
+    A.aqs_set_kernel_timing(True)
+    l0 = A.aqs_launch_count()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record()
+        res = b.minimize(A.fire_params(max_iter=budget), check_status=False)
+        e1.record()
+        e1.synchronize()
+    st = A.aqs_get_kernel_stats()
+    A.aqs_set_kernel_timing(False)
+    secs = e0.elapsed_time(e1) / 1e3
+    iters = sum(r["iters"] for r in res)
+    kern_s = st["kernel_ms"] / 1e3
+    # algorithmic bytes of the FP32 force evaluations: 4 B per list entry
+    # (the lists, ~0.4 GB per replica set, stream from HBM) plus 28 B per atom
+    # (its 16-byte position record and 12-byte FP32 force); neighbour records
+    # are gathered from cell-sorted storage and are not counted
+    algo_bytes = 4.0 * st["pairs32"] + 28.0 * n * st["evals32"]
+    gbs = algo_bytes / kern_s / 1e9 if kern_s else 0.0
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    config = {"workload": "3D binary LJ glass (80:20, rho=1.2), N=65536, 32 level-I "
+                          "predictions (K=20, dgamma=5e-5) minimised as one batch for a bounded "
+                          "number of FIRE iterations, mixed precision",
+              "n_atoms": n, "P": P, "K": K, "dgamma": dg, "fire_iterations_budget": budget,
+              "l2": "working set (~%d MB of lists) exceeds L2" % int(4 * nb * n * P / 1e6)}
+    _line("FIRE iterations/s (3D, 32 x 65536 atoms)", iters / secs, "iterations/s", args,
+          1e3 * secs, config,
+          {"gpu_launches": A.aqs_launch_count() - l0, "clocks": clk.summary(),
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                        "frac": gbs / peak, "traffic": None,
+                        "note": "algorithmic bytes = 4 per list entry visited + 28 per atom per FP32 evaluation"},
+           "detail": {"mean_neighbours": nb, "quench_iters": q["iters"],
+                      "quench_fmax": q["fmax"], "fp32_evals": st["evals32"],
+                      "fp64_evals": st["evals64"], "cluster_size": b.cluster_size(0)}})
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,9 +316,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--baseline-steps", type=int, default=2)
+    ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d"], default="cfg1")
+    ap.add_argument("--quench-iters", type=int, default=400000)
+    ap.add_argument("--iters3d", type=int, default=2000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch64(args) or 0
+    if args.workload == "glass3d":
+        return run_glass3d(args) or 0
 
     import torch
     ws, rank, local = _dist()
@@ -254,16 +394,7 @@ def main():
     st = A.aqs_get_kernel_stats()
     clocks = clk.summary()
 
-    secs = dev_ms / 1e3
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([secs, float(accepted)], device="cuda", dtype=torch.float64)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        total_steps, secs = float(tt[1]), float(mx[0])
-    else:
-        total_steps = float(accepted)
+    total_steps, secs = combine_ranks(dev_ms / 1e3, accepted, "cuda")
     value = total_steps / secs
 
     # ---------------- end to end through the C ABI with host buffers

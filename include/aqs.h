@@ -309,6 +309,30 @@ aqs_status aqs_energy_forces_noalloc(int dim, int64_t n, const double* pos, cons
                                      const double* box, const aqs_potential* pot, double* forces,
                                      double* energy_tau, void* stream);
 
+/* ---- cluster-size autotuner ----
+ * The paper runs one chain per CPU thread (Sec. 3.3); here every replica is
+ * minimised by one thread-block cluster of C CTAs, and C trades atoms per
+ * thread against how many replicas are resident at once.  The tuner times
+ * `iters` FIRE iterations (convergence test disabled, so every candidate does
+ * the same work from the same configuration) of the replicas with mask[r] != 0
+ * (NULL = all) for every feasible C in 1..16 (at most 4096 and at least 32
+ * atoms per CTA, and at least one cluster resident), keeps the fastest for
+ * those replicas and returns it in *best_cluster (may be NULL).
+ * ms_per_iter (may be NULL) receives 17 values: entry C is the measured wall
+ * time per iteration of that candidate in milliseconds, -1 where C was not
+ * feasible, entry 0 unused.  Positions, boxes and minimiser state are restored
+ * afterwards, so tuning does not change the configuration.  Errors as
+ * aqs_minimize, except that not converging is the expected outcome. */
+aqs_status aqs_autotune_clusters(aqs_system* sys, const aqs_fire_params* fire, int64_t iters,
+                                 const uint8_t* mask, int* best_cluster, double* ms_per_iter);
+/* With iters > 0, every later minimisation (aqs_minimize, aqs_run_sequential,
+ * the chains of aqs_parallel_step) first tunes the cluster size for its set of
+ * replicas in flight, once per (number of replicas, largest N), and reuses the
+ * cached choice afterwards.  0 switches it off (the default size rule:
+ * C = min(16, 152 / replicas), at least ceil(N / 4096)).  Ignored when the
+ * system was created with an explicit cluster_size. */
+aqs_status aqs_set_autotune(aqs_system* sys, int64_t iters);
+
 /* ---- diagnostics ---- */
 /* Counters of the persistent minimiser kernel, accumulated over all systems
  * while timing is on (aqs_set_kernel_timing(1)); pair visits count one atom

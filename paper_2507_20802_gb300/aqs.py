@@ -126,6 +126,10 @@ _SIGS = {
     "aqs_energy_forces_noalloc": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_void_p,
                                             C.POINTER(C.c_double), C.POINTER(aqs_potential),
                                             C.c_void_p, C.c_void_p, C.c_void_p]),
+    "aqs_autotune_clusters": (C.c_int, [C.c_void_p, C.POINTER(aqs_fire_params), C.c_int64,
+                                        C.POINTER(C.c_uint8), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_double)]),
+    "aqs_set_autotune": (C.c_int, [C.c_void_p, C.c_int64]),
     "aqs_set_kernel_timing": (None, [C.c_int]),
     "aqs_get_kernel_stats": (None, [C.POINTER(aqs_kernel_stats)]),
     "aqs_reset_kernel_stats": (None, []),
@@ -486,3 +490,19 @@ class System:
 
     def cluster_size(self, replica=0):
         return lib().aqs_cluster_size(self.h, replica)
+
+    def autotune(self, iters=200, fire=None, mask=None):
+        """Times every feasible cluster size on `iters` FIRE iterations and
+        keeps the fastest; returns (best C, {C: ms per iteration})."""
+        best = C.c_int(0)
+        ms = np.zeros(17)
+        m = None
+        if mask is not None:
+            mk = np.ascontiguousarray(mask, dtype=np.uint8)
+            m = mk.ctypes.data_as(C.POINTER(C.c_uint8))
+        check(lib().aqs_autotune_clusters(self.h, C.byref(fire or fire_params()), C.c_int64(iters),
+                                          m, C.byref(best), _dp(ms)))
+        return best.value, {c: float(ms[c]) for c in range(1, 17) if ms[c] >= 0}
+
+    def set_autotune(self, iters):
+        check(lib().aqs_set_autotune(self.h, C.c_int64(iters)))

@@ -184,6 +184,9 @@ __device__ __forceinline__ float nmaxf(float a, float b) { return (a != a || a >
 // While the largest FP64 force exceeds this, mixed mode keeps evaluating in
 // FP64 (random starts and collisions), where FP32 would overflow.
 constexpr double kBigForce = 1e3;
+// FP32 moves also need |v|^2 (summed over the replica) below this, so that
+// velocities, powers and their float-float sums stay inside the FP32 range
+constexpr double kBigV2 = 1e30;
 
 // MEM: 0 = list in global memory, neighbour positions gathered from the owner
 // CTA's shared memory (DSMEM); 1 = list staged in shared memory, DSMEM
@@ -267,6 +270,9 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   const double vol = D == 2 ? H[0] * H[3] : H[0] * H[4] * H[8];
   bool want_e = MIXED;  // mixed: every FP64 evaluation also gives E and tau
   float wmaxf = 0.0f;   // max |x_ref - x_b| at the last FP64 evaluation (mixed)
+  // mixed: true while A.v holds the current velocity in FP64 (moves after FP64
+  // evaluations), false while the FP32 registers v32 do (moves after FP32 ones)
+  bool v64 = true;
   double gamma_term = 0.0;
   float gamma_termf = 0.0f;
   const float skinf = (float)A.skin;
@@ -571,6 +577,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
       npos = 0;
       iters = evals = evals32 = 0;
       want_e = MIXED;
+      v64 = true;
       phase = 1;
       make_tables();
     }
@@ -626,7 +633,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         double f2 = 0.0, pv = 0.0, v2 = 0.0, u2 = 0.0;
 #pragma unroll
         for (int c = 0; c < D; c++) {
-          double vc = MIXED ? (double)v32[k][c] : A.v[c * N + gi];
+          double vc = (MIXED && !v64) ? (double)v32[k][c] : A.v[c * N + gi];
           f2 = fma(F[k][c], F[k][c], f2);
           pv = fma(F[k][c], vc, pv);
           v2 = fma(vc, vc, v2);
@@ -862,7 +869,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
           }
           iters++;
           acc_it++;
-          mode = (was64 && fmx > kBigForce) ? kModeEval64 : kModeDev;
+          mode = (was64 && (fmx > kBigForce || T[3] > kBigV2)) ? kModeEval64 : kModeDev;
         } else if (!stop) {
           mode = kModeEval64;
         }
@@ -943,17 +950,20 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
     if (c.move) {
       // ================= FIRE update =================
       if (MIXED && c.was64) {
-        // step after an FP64 evaluation: FP64 arithmetic (forces may be huge)
+        // step after an FP64 evaluation: FP64 arithmetic and an FP64 velocity
+        // (forces and velocities may exceed the FP32 range)
 #pragma unroll
         for (int k = 0; k < APT; k++) {
           int li = tid + k * nthr;
           if (li >= cnt) continue;
+          const int64_t gv = base + li;
           double sv[3], mx = 0.0;
 #pragma unroll
           for (int cc = 0; cc < D; cc++) {
-            double vc = c.reset ? 0.0 : (double)v32[k][cc];
+            double vc = c.reset ? 0.0 : (v64 ? A.v[cc * N + gv] : (double)v32[k][cc]);
             vc = fma(c.keep, fma(c.dt, F[k][cc], vc), c.ratio * F[k][cc]);
-            v32[k][cc] = (float)vc;
+            A.v[cc * N + gv] = vc;
+            v32[k][cc] = (float)vc;  // used only once |v|^2 < kBigV2
             sv[cc] = c.dt * vc;
             mx = fmax(mx, fabs(sv[cc]));
           }
@@ -978,7 +988,9 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
             publish64(k);
           }
         }
+        v64 = true;
       } else if (MIXED) {
+        v64 = false;
         const float dtf = c.dtf, kf = c.keepf, rf = c.ratiof;
         const float ms = (float)fp.max_step;
 #pragma unroll
@@ -1158,7 +1170,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   }
 
   // ---- exit: keep v for a resumed minimisation, store the job state ----
-  if (MIXED && phase == 1) {
+  if (MIXED && phase == 1 && !v64) {
 #pragma unroll
     for (int k = 0; k < APT; k++) {
       int li = tid + k * nthr;

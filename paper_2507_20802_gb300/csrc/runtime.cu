@@ -5,12 +5,15 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstddef>
 #include <cstring>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "aqs_internal.cuh"
@@ -59,6 +62,11 @@ struct Alloc {
 
 struct aqs_system {
   int dim = 2, R = 0, nt = 0, prec = 0, cap = 0, C_override = 0;
+  // cluster-size autotuner: iterations per candidate (0 = off) and the
+  // choices made so far, keyed by (replicas in flight, largest N)
+  int64_t tune_iters = 0;
+  bool tuning = false;
+  std::map<std::pair<int, int64_t>, int> tuned;
   aqs_potential pot{};
   double skin = 0.3, rcmax = 0.0, rlist = 0.0;
   cudaStream_t stream = nullptr;
@@ -493,11 +501,37 @@ aqs_status ensure_records(aqs_system* s, int64_t nsteps, bool snap) {
   return AQS_OK;
 }
 
+aqs_status tune_clusters(aqs_system* s, const aqs_fire_params* f, const std::vector<uint8_t>& mask,
+                         int64_t iters, int* best, double* ms_per_iter);
+aqs_status apply_cluster(aqs_system* s, const std::vector<int>& reps, int C);
+
 // Runs the jobs of the replicas with jobs[r].nsteps > 0 to completion in
 // persistent launches (one per cluster size and pass); between passes only
 // list rebuilds and budget yields are handled on the host.
 aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<Job>& jobs,
                     JobOut* out, const float* warm_u = nullptr) {
+  if (s->tune_iters > 0 && s->C_override <= 0 && !s->tuning) {
+    std::vector<uint8_t> mask(s->R, 0);
+    std::vector<int> reps;
+    int64_t nmax = 0;
+    for (int r = 0; r < s->R; r++)
+      if (jobs[r].nsteps > 0) {
+        mask[r] = 1;
+        reps.push_back(r);
+        nmax = std::max(nmax, s->n[r]);
+      }
+    if (!reps.empty()) {
+      const auto key = std::make_pair((int)reps.size(), nmax);
+      auto it = s->tuned.find(key);
+      if (it == s->tuned.end()) {
+        int best = 0;
+        AQS_TRY(tune_clusters(s, f, mask, s->tune_iters, &best, nullptr));
+        s->tuned[key] = best;
+      } else {
+        AQS_TRY(apply_cluster(s, reps, it->second));
+      }
+    }
+  }
   int64_t maxsteps = 0;
   bool snap = false;
   std::vector<int> todo;
@@ -870,6 +904,7 @@ aqs_status ensure_chains(aqs_system* s, int src, int P) {
     destroy(c);
     return fail(AQS_ERR_OOM, "chain snapshot allocation failed");
   }
+  c->tune_iters = s->tune_iters;
   s->chains = c;
   return AQS_OK;
 }
@@ -1354,6 +1389,35 @@ int aqs_cluster_size(const aqs_system* s, int r) {
   return (s && r >= 0 && r < s->R) ? s->geom[r].C : 0;
 }
 
+aqs_status aqs_autotune_clusters(aqs_system* s, const aqs_fire_params* f, int64_t iters,
+                                 const uint8_t* mask, int* best_cluster, double* ms_per_iter) {
+  if (!s || !f || iters <= 0) return fail(AQS_ERR_INVALID_ARG, "autotune: bad arguments");
+  if (s->C_override > 0)
+    return fail(AQS_ERR_INVALID_ARG, "autotune: the system has an explicit cluster size");
+  std::vector<uint8_t> m(s->R, 1);
+  if (mask)
+    for (int r = 0; r < s->R; r++) m[r] = mask[r] ? 1 : 0;
+  int best = 0;
+  AQS_TRY(tune_clusters(s, f, m, iters, &best, ms_per_iter));
+  int64_t nmax = 0;
+  int cnt = 0;
+  for (int r = 0; r < s->R; r++)
+    if (m[r]) {
+      nmax = std::max(nmax, s->n[r]);
+      cnt++;
+    }
+  if (best > 0) s->tuned[std::make_pair(cnt, nmax)] = best;
+  if (best_cluster) *best_cluster = best;
+  return AQS_OK;
+}
+
+aqs_status aqs_set_autotune(aqs_system* s, int64_t iters) {
+  if (!s || iters < 0) return fail(AQS_ERR_INVALID_ARG, "set_autotune: bad arguments");
+  s->tune_iters = iters;
+  if (s->chains) s->chains->tune_iters = iters;
+  return AQS_OK;
+}
+
 }  // extern "C"
 
 // =====================================================================
@@ -1486,6 +1550,114 @@ aqs_status restore_positions(aqs_system* s, const std::vector<uint8_t>& which,
   sync_tilt_to_state(s);
   AQS_TRY(upload_state(s));
   return rebuild(s, which);
+}
+
+// Sets the cluster size of the replicas `reps` to C and rebuilds their lists
+// (list entries encode the owner CTA of every neighbour).
+aqs_status apply_cluster(aqs_system* s, const std::vector<int>& reps, int C) {
+  std::vector<uint8_t> flags(s->R, 0);
+  bool any = false;
+  for (int r : reps) {
+    if (s->geom[r].C == C) continue;
+    s->geom[r].C = C;
+    s->geom[r].npc = (int)((s->n[r] + C - 1) / C);
+    flags[r] = 1;
+    any = true;
+  }
+  return any ? rebuild(s, flags) : AQS_OK;
+}
+
+bool cluster_feasible(const aqs_system* s, const std::vector<int>& reps, int C) {
+  for (int r : reps) {
+    const int64_t npc = (s->n[r] + C - 1) / C;
+    if (npc > 4096 || (C > 1 && s->n[r] < 32 * (int64_t)C)) return false;
+    if (minimize_max_active_clusters(s->dim, s->prec == AQS_MIXED, C, (int)npc, (int)s->n[r],
+                                     s->nt, s->cap) <= 0)
+      return false;
+  }
+  return true;
+}
+
+// Times `iters` FIRE iterations (convergence test off) of the masked replicas
+// for every feasible cluster size and keeps the fastest; the configuration
+// and the host-side minimiser state are restored after every candidate.
+aqs_status tune_clusters(aqs_system* s, const aqs_fire_params* f, const std::vector<uint8_t>& mask,
+                         int64_t iters, int* best, double* ms_per_iter) {
+  std::vector<int> reps;
+  for (int r = 0; r < s->R; r++)
+    if (mask[r]) reps.push_back(r);
+  if (ms_per_iter)
+    for (int c = 0; c <= kMaxCluster; c++) ms_per_iter[c] = -1.0;
+  if (best) *best = 0;
+  if (reps.empty() || iters <= 0) return AQS_OK;
+  if (!s->d_save) AQS_TRY(alloc_arr(s, &s->d_save, (size_t)s->ntot * s->dim));
+  AQS_TRY(save_positions(s));
+  std::vector<double> tilt(s->R);
+  std::vector<int> c0(s->R);
+  for (int r = 0; r < s->R; r++) {
+    tilt[r] = s->geom[r].H[1];
+    c0[r] = s->geom[r].C;
+  }
+  const std::vector<RepState> st0 = s->st;
+  aqs_fire_params ft = *f;
+  ft.tol = 0.0;
+  ft.max_iter = iters;
+  aqs_fire_params fw = ft;
+  fw.max_iter = std::min<int64_t>(iters, 32);
+  const int saved_override = s->C_override;
+  s->tuning = true;
+  int bestC = 0;
+  double bestT = 1e300;
+  aqs_status err = AQS_OK;
+  for (int C = 1; C <= kMaxCluster && err == AQS_OK; C++) {
+    if (!cluster_feasible(s, reps, C)) continue;
+    s->C_override = C;  // no cluster growth while a candidate is timed
+    if ((err = apply_cluster(s, reps, C)) != AQS_OK) break;
+    // untimed first launch of this kernel instance
+    aqs_status st = minimize_impl(s, &fw, mask, nullptr);
+    if (st != AQS_OK && st != AQS_ERR_NOT_CONVERGED) {
+      err = st;
+      break;
+    }
+    if ((err = restore_positions(s, mask, tilt)) != AQS_OK) break;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
+      err = fail(AQS_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    st = minimize_impl(s, &ft, mask, nullptr);
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
+      err = fail(AQS_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    const auto t1 = std::chrono::steady_clock::now();
+    if (st != AQS_OK && st != AQS_ERR_NOT_CONVERGED) {
+      err = st;
+      break;
+    }
+    int64_t it = 1;
+    for (int r : reps) it = std::max<int64_t>(it, s->st[r].iters);
+    const double ms = std::chrono::duration<double, std::milli>(t1 - t0).count() / (double)it;
+    if (ms_per_iter) ms_per_iter[C] = ms;
+    if (ms < bestT) {
+      bestT = ms;
+      bestC = C;
+    }
+    err = restore_positions(s, mask, tilt);
+  }
+  s->tuning = false;
+  s->C_override = saved_override;
+  for (int r : reps) {
+    const int C = (err == AQS_OK && bestC > 0) ? bestC : c0[r];
+    s->geom[r].C = C;
+    s->geom[r].npc = (int)((s->n[r] + C - 1) / C);
+  }
+  s->st = st0;
+  const aqs_status rs = restore_positions(s, mask, tilt);
+  if (err != AQS_OK) return err;
+  if (rs != AQS_OK) return rs;
+  if (best) *best = bestC;
+  return AQS_OK;
 }
 
 }  // namespace
