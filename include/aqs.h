@@ -309,29 +309,47 @@ aqs_status aqs_energy_forces_noalloc(int dim, int64_t n, const double* pos, cons
                                      const double* box, const aqs_potential* pot, double* forces,
                                      double* energy_tau, void* stream);
 
-/* ---- cluster-size autotuner ----
+/* ---- launch configuration: cluster size, staging mode, autotuner ----
  * The paper runs one chain per CPU thread (Sec. 3.3); here every replica is
  * minimised by one thread-block cluster of C CTAs, and C trades atoms per
- * thread against how many replicas are resident at once.  The tuner times
- * `iters` FIRE iterations (convergence test disabled, so every candidate does
- * the same work from the same configuration) of the replicas with mask[r] != 0
- * (NULL = all) for every feasible C in 1..16 (at most 4096 and at least 32
- * atoms per CTA, and at least one cluster resident), keeps the fastest for
- * those replicas and returns it in *best_cluster (may be NULL).
- * ms_per_iter (may be NULL) receives 17 values: entry C is the measured wall
- * time per iteration of that candidate in milliseconds, -1 where C was not
- * feasible, entry 0 unused.  Positions, boxes and minimiser state are restored
- * afterwards, so tuning does not change the configuration.  Errors as
- * aqs_minimize, except that not converging is the expected outcome. */
+ * thread against how many replicas are resident at once.  The staging mode
+ * says where a CTA finds its list rows and its neighbours' position records:
+ *   0  rows from global memory each iteration, records from global memory
+ *   1  rows staged in shared memory, records read from the owner CTA (DSMEM)
+ *   2  rows staged, the whole replica's records copied into shared memory
+ *   3  rows staged, records from global memory
+ * Every mode reads the same values, so results are bitwise identical; only
+ * speed and shared-memory needs differ (a mode that does not fit falls back
+ * to the automatic choice: 2, else 1, else 0). */
+
+/* Times `iters` FIRE iterations (convergence test disabled, so every candidate
+ * does the same work from the same configuration) of the replicas with
+ * mask[r] != 0 (NULL = all): first every feasible C in 1..16 (at most 4096 and
+ * at least 32 atoms per CTA, at least one cluster resident) with automatic
+ * staging, then every staging mode that fits at the fastest C.  Keeps the
+ * fastest pair for those replicas (unless aqs_set_staging fixed the mode).
+ * Outputs, each may be NULL: *best_cluster, *best_staging (-1 = automatic);
+ * ms_per_iter[17] (entry C: wall time per iteration in ms, -1 if C was not
+ * feasible; entry 0 unused); ms_per_staging[4] (entry m: time per iteration
+ * at the best C in mode m, -1 if not timed).  Positions, boxes and minimiser
+ * state are restored afterwards, so tuning does not change the
+ * configuration.  Errors as aqs_minimize, except that not converging is the
+ * expected outcome. */
 aqs_status aqs_autotune_clusters(aqs_system* sys, const aqs_fire_params* fire, int64_t iters,
-                                 const uint8_t* mask, int* best_cluster, double* ms_per_iter);
+                                 const uint8_t* mask, int* best_cluster, int* best_staging,
+                                 double* ms_per_iter, double* ms_per_staging);
 /* With iters > 0, every later minimisation (aqs_minimize, aqs_run_sequential,
- * the chains of aqs_parallel_step) first tunes the cluster size for its set of
- * replicas in flight, once per (number of replicas, largest N), and reuses the
- * cached choice afterwards.  0 switches it off (the default size rule:
- * C = min(16, 152 / replicas), at least ceil(N / 4096)).  Ignored when the
- * system was created with an explicit cluster_size. */
+ * the chains of aqs_parallel_step) first tunes cluster size and staging for
+ * its set of replicas in flight, once per (number of replicas, largest N),
+ * and reuses the cached choice afterwards.  0 switches it off (the default
+ * size rule: C = min(16, 152 / replicas), at least ceil(N / 4096)).  Ignored
+ * when the system was created with an explicit cluster_size. */
 aqs_status aqs_set_autotune(aqs_system* sys, int64_t iters);
+/* Fixes the staging mode (0..3) of this system and its chains, or -1 for the
+ * automatic choice.  AQS_ERR_INVALID_ARG outside -1..3. */
+aqs_status aqs_set_staging(aqs_system* sys, int mode);
+/* Staging mode a launch of this replica alone would use (-1 on a bad argument). */
+int aqs_staging(const aqs_system* sys, int replica);
 
 /* ---- diagnostics ---- */
 /* Counters of the persistent minimiser kernel, accumulated over all systems
@@ -345,6 +363,7 @@ typedef struct {
   int64_t pairs32;       /* pair visits in FP32 evaluations */
   int64_t pairs64;       /* pair visits in FP64 evaluations */
   int64_t atom_iters;    /* atoms x FIRE iterations */
+  int64_t rebuilds;      /* Verlet-list rebuilds done inside the minimiser kernel */
 } aqs_kernel_stats;
 void aqs_set_kernel_timing(int on);
 void aqs_get_kernel_stats(aqs_kernel_stats* out);

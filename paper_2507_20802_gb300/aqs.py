@@ -78,7 +78,7 @@ class aqs_parallel_result(C.Structure):
 class aqs_kernel_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("kernel_ms", C.c_double), ("evals32", C.c_int64),
                 ("evals64", C.c_int64), ("pairs32", C.c_int64), ("pairs64", C.c_int64),
-                ("atom_iters", C.c_int64)]
+                ("atom_iters", C.c_int64), ("rebuilds", C.c_int64)]
 
 
 # exported symbols and their signatures (kept in the order of include/aqs.h)
@@ -128,8 +128,11 @@ _SIGS = {
                                             C.c_void_p, C.c_void_p, C.c_void_p]),
     "aqs_autotune_clusters": (C.c_int, [C.c_void_p, C.POINTER(aqs_fire_params), C.c_int64,
                                         C.POINTER(C.c_uint8), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]),
     "aqs_set_autotune": (C.c_int, [C.c_void_p, C.c_int64]),
+    "aqs_set_staging": (C.c_int, [C.c_void_p, C.c_int]),
+    "aqs_staging": (C.c_int, [C.c_void_p, C.c_int]),
     "aqs_set_kernel_timing": (None, [C.c_int]),
     "aqs_get_kernel_stats": (None, [C.POINTER(aqs_kernel_stats)]),
     "aqs_reset_kernel_stats": (None, []),
@@ -492,17 +495,26 @@ class System:
         return lib().aqs_cluster_size(self.h, replica)
 
     def autotune(self, iters=200, fire=None, mask=None):
-        """Times every feasible cluster size on `iters` FIRE iterations and
-        keeps the fastest; returns (best C, {C: ms per iteration})."""
-        best = C.c_int(0)
+        """Times every feasible cluster size, then every staging mode at the
+        fastest size, on `iters` FIRE iterations and keeps the fastest.
+        Returns (C, staging, {C: ms per iteration}, {mode: ms per iteration})."""
+        best, mode = C.c_int(0), C.c_int(-1)
         ms = np.zeros(17)
+        mm = np.zeros(4)
         m = None
         if mask is not None:
             mk = np.ascontiguousarray(mask, dtype=np.uint8)
             m = mk.ctypes.data_as(C.POINTER(C.c_uint8))
         check(lib().aqs_autotune_clusters(self.h, C.byref(fire or fire_params()), C.c_int64(iters),
-                                          m, C.byref(best), _dp(ms)))
-        return best.value, {c: float(ms[c]) for c in range(1, 17) if ms[c] >= 0}
+                                          m, C.byref(best), C.byref(mode), _dp(ms), _dp(mm)))
+        return (best.value, mode.value, {c: float(ms[c]) for c in range(1, 17) if ms[c] >= 0},
+                {k: float(mm[k]) for k in range(4) if mm[k] >= 0})
+
+    def set_staging(self, mode):
+        check(lib().aqs_set_staging(self.h, int(mode)))
+
+    def staging(self, replica=0):
+        return lib().aqs_staging(self.h, replica)
 
     def set_autotune(self, iters):
         check(lib().aqs_set_autotune(self.h, C.c_int64(iters)))

@@ -68,7 +68,7 @@ struct RepState {
   int phase;        // 0: next step not started, 1: FIRE in progress
   int first_noaffine;
   int want_snap;    // write the positions after the first (no-affine) step
-  int pad;
+  int kreb;         // Verlet rebuilds done inside the kernel (monotonic)
 };
 
 // per converged step the kernel records: E, tau, D_k (from the affine start), FIRE

@@ -3,8 +3,11 @@
 //
 // Each replica is owned by a cluster of C CTAs (C <= 16); CTA `rank` owns the
 // atoms [rank * npc, (rank + 1) * npc) of the replica's cell-sorted order and
-// publishes their positions in its shared memory.  Neighbour positions are
-// read through distributed shared memory (DSMEM) of the owning CTA.  One FIRE
+// publishes their positions in its shared memory (and, in staging modes 0 and
+// 3, in a global record array).  Neighbour positions are read from the owner
+// CTA through distributed shared memory (DSMEM), from a shared-memory copy of
+// the whole replica, or from the global records (the staging modes listed in
+// minimize.cuh).  One FIRE
 // iteration is:
 //   force phase   -- pair forces of the owned atoms from the Verlet list,
 //                    per-thread partial sums of the FIRE reductions;
@@ -38,9 +41,20 @@ size_t minimize_smem_bytes(int dim, int npc, int nrep, int nt, int cap, int mem)
   return minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, mem);
 }
 
+int minimize_atoms_per_thread(int npc) {
+  int apt = 0, threads = 0;
+  choose_apt(npc, &apt, &threads);
+  return apt;
+}
+
+int minimize_staging(int dim, int npc, int nrep, int nt, int cap, int want) {
+  return choose_mem(dim, npc, nrep, nt, cap, want);
+}
+
 static cudaError_t dispatch(int dim, bool mixed, const MinArgs* a, int n_clusters, int C, int npc,
-                            int nrep, int nt, int cap, cudaStream_t s, int* max_clusters) {
-  int mem = choose_mem(dim, npc, nrep, nt, cap);
+                            int nrep, int nt, int cap, cudaStream_t s, int* max_clusters,
+                            int staging) {
+  int mem = choose_mem(dim, npc, nrep, nt, cap, staging);
   size_t smem = minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, mem);
   if (dim == 2)
     return mixed ? run_mem_2_mixed(mem, a, n_clusters, C, npc, smem, s, max_clusters)
@@ -50,15 +64,17 @@ static cudaError_t dispatch(int dim, bool mixed, const MinArgs* a, int n_cluster
 }
 
 cudaError_t launch_minimize(int dim, bool mixed, MinArgs a, int n_clusters, int C, int npc,
-                            int nrep, int cap, cudaStream_t s) {
+                            int nrep, int cap, cudaStream_t s, int staging) {
   a.npc_launch = npc;
   a.nrep_launch = nrep;
-  return dispatch(dim, mixed, &a, n_clusters, C, npc, nrep, a.nt, cap, s, nullptr);
+  return dispatch(dim, mixed, &a, n_clusters, C, npc, nrep, a.nt, cap, s, nullptr, staging);
 }
 
-int minimize_max_active_clusters(int dim, bool mixed, int C, int npc, int nrep, int nt, int cap) {
+int minimize_max_active_clusters(int dim, bool mixed, int C, int npc, int nrep, int nt, int cap,
+                                 int staging) {
   int m = 0;
-  if (dispatch(dim, mixed, nullptr, 1, C, npc, nrep, nt, cap, nullptr, &m) != cudaSuccess) {
+  if (dispatch(dim, mixed, nullptr, 1, C, npc, nrep, nt, cap, nullptr, &m, staging) !=
+      cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

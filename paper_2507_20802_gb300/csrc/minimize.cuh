@@ -41,12 +41,39 @@ struct MinArgs {
                           // within each replica (nullable)
   int npc_launch;         // shared-memory stride (largest npc of the launch)
   int nrep_launch;        // largest replica of the launch (staged positions)
+  // [ntot] position records in global memory (Pub<D>, 16 B in 2D, 32 B in 3D),
+  // the source of neighbour records in staging modes 0 and 3
+  void* pubg;
+  // per-atom state of launches with 4 or 8 atoms per thread (allocated on
+  // first use): [5][3][ntot] FP32 (q_ref, delta, v, f_ref, f_used) and
+  // [3][ntot] FP64 force
+  float* lean32;
+  double* lean64;
 };
 
+// Staging modes of the minimiser (where a CTA finds list rows and the
+// published position records of its neighbours):
+//   0: rows read from global memory each iteration, records from global memory
+//   1: rows staged in shared memory, records read from the owner CTA (DSMEM)
+//   2: rows staged, records of the whole replica copied into shared memory
+//      from the owner CTAs each iteration
+//   3: rows staged, records from global memory
+// All modes read bitwise identical values, so they give identical results.
+constexpr int kNumStaging = 4;
+
 size_t minimize_smem_bytes(int dim, int npc, int nrep, int nt, int cap, int mem);
+// staging mode used for this configuration: `want` if it fits in shared
+// memory (want in 0..3), else the automatic choice (2, then 1, then 0)
+int minimize_staging(int dim, int npc, int nrep, int nt, int cap, int want);
 cudaError_t launch_minimize(int dim, bool mixed, MinArgs a, int n_clusters, int C, int npc,
-                            int nrep, int cap, cudaStream_t s);
+                            int nrep, int cap, cudaStream_t s, int staging = -1);
+// atoms per thread of a launch with npc atoms per CTA (1, 2, 4 or 8)
+int minimize_atoms_per_thread(int npc);
+// launches that keep the per-atom state in MinArgs::lean32 / lean64 instead
+// of registers (where registers would spill)
+constexpr bool minimize_is_lean(int dim, int apt) { return apt >= 4 || (dim == 3 && apt >= 2); }
 // clusters of C CTAs that can be resident at once for this configuration
-int minimize_max_active_clusters(int dim, bool mixed, int C, int npc, int nrep, int nt, int cap);
+int minimize_max_active_clusters(int dim, bool mixed, int C, int npc, int nrep, int nt, int cap,
+                                 int staging = -1);
 
 }  // namespace aqs

@@ -41,8 +41,14 @@ __device__ __forceinline__ void pair64(const PairCoef& c, const double* d, doubl
   }
 }
 
+// FP32 coefficients of one species pair, held in registers by the pair loop
+struct Coef32 {
+  float Af, Bf, Cf, rc2f;
+};
+__device__ __forceinline__ Coef32 coef32(const PairCoef& c) { return Coef32{c.Af, c.Bf, c.Cf, c.rc2f}; }
+
 // phi(s) in FP32
-__device__ __forceinline__ float phi32(const PairCoef& c, float s) {
+__device__ __forceinline__ float phi32(const Coef32& c, float s) {
   float a = rsqrtf(s);
   float u = a * a;
   float u2 = u * u, u4 = u2 * u2, u7 = u4 * u2 * u;
@@ -56,7 +62,7 @@ __device__ __forceinline__ float phi32(const PairCoef& c, float s) {
 //   (s^-1/2 - s0^-1/2) / ds = -(ab)^2 / (a + b),  a = s^-1/2, b = s0^-1/2
 //   dF = phi(s) e + [phi(s) - phi(s0)] d0
 template <int D>
-__device__ __forceinline__ void pair_dev(const PairCoef& c, const float* d0, const float* e,
+__device__ __forceinline__ void pair_dev(const Coef32& c, const float* d0, const float* e,
                                          float* F) {
   float s0 = d0[0] * d0[0], ds = e[0] * fmaf(2.0f, d0[0], e[0]);
 #pragma unroll
@@ -150,6 +156,11 @@ __device__ __forceinline__ void load_pub64(const Pub<D>* p, double* q) {
 
 constexpr int kModeEval64 = 0, kModeDev = 1;
 
+// Cell-image offsets of the FP32 pair loop, one copy per lane
+// ([code * 3 + axis][32]): every lane reads its own bank, so the per-pair
+// table lookup has no bank conflicts whatever codes the lanes need.
+constexpr int kOffLane = 27 * 3 * 32;
+
 // Control block written once per iteration by thread 0 of every CTA (all CTAs
 // compute it from bitwise identical totals) and read by the CTA's threads.
 struct Ctl {
@@ -209,7 +220,9 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
   const int64_t N = A.ntot;
   const int lstride = A.npc_launch;
-  constexpr bool LSM = MEM >= 1;
+  constexpr bool LSM = MEM >= 1;                // list rows staged in shared memory
+  constexpr bool GREC = MEM == 0 || MEM == 3;   // neighbour records from global memory
+  Pub<D>* pubg = reinterpret_cast<Pub<D>*>(A.pubg);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Pub<D>* pub = reinterpret_cast<Pub<D>*>(smem_raw);  // MEM 2: whole replica, else own atoms
@@ -219,7 +232,8 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   double* wred = red + kNumRed;                                                   // [32][kNumRed]
   double* off64 = wred + 32 * kNumRed;                                            // [27][3]
   float* off32 = reinterpret_cast<float*>(off64 + 27 * 3);                        // [27][3]
-  PairCoef* coef = reinterpret_cast<PairCoef*>(off32 + 27 * 3 + 3);               // [nt*nt]
+  float* off32l = off32 + 27 * 3 + 3;                                             // [27*3][32]
+  PairCoef* coef = reinterpret_cast<PairCoef*>(off32l + kOffLane);                // [nt*nt]
   uint32_t* lst = reinterpret_cast<uint32_t*>(coef + A.nt * A.nt);                // [cap][lstride]
   __shared__ Pub<D>* rpub[kMaxCluster];
   __shared__ double* rred[kMaxCluster];
@@ -244,6 +258,11 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         off32[tid * 3 + k] = (float)o[k];
       }
     }
+    for (int i = tid; i < ncode * 32; i += nthr) {
+      double o[3];
+      cell_offset<D>(H, g.nc, i >> 5, o);
+      for (int k = 0; k < D; k++) off32l[((i >> 5) * 3 + k) * 32 + (i & 31)] = (float)o[k];
+    }
   };
   make_tables();
   for (int k = tid; k < A.nt * A.nt; k += nthr) coef[k] = A.coef[k];
@@ -267,6 +286,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   int64_t iters = st->iters, evals = st->evals64, evals32 = st->evals32;
   int64_t launch_iters = 0;
   int64_t acc_it = st->acc_iters, acc64 = st->acc64, acc32 = st->acc32;
+  int kreb = st->kreb;
   const double vol = D == 2 ? H[0] * H[3] : H[0] * H[4] * H[8];
   bool want_e = MIXED;  // mixed: every FP64 evaluation also gives E and tau
   float wmaxf = 0.0f;   // max |x_ref - x_b| at the last FP64 evaluation (mixed)
@@ -282,19 +302,66 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   int status = kStatusRunning;
   double E = 0.0, W = 0.0, fmx = 0.0;
 
+  // Per-atom state.  With few atoms per thread it lives in registers; with
+  // more ("lean" launches: 4 or 8 atoms per thread, 2 or more in 3D)
+  // registers would spill, so it lives in global memory (L2) and only the
+  // atom being processed is in registers: FP32 reference position, displacement, velocity, reference
+  // force and the force used by the update, and the FP64 force.
+  constexpr bool LEAN = minimize_is_lean(D, APT);
+  constexpr int AR = LEAN ? 1 : APT;
   int ty[APT];
-  float q32[APT][3], d32[APT][3], v32[APT][3], fr32[APT][3];
+  float q32[AR][3], d32[AR][3], v32[AR][3], fr32[AR][3], Fu[AR][3];
+  double F[AR][3];
+  float* const l32 = A.lean32;   // [5][3][ntot]: q, delta, v, f_ref, f_used
+  double* const l64 = A.lean64;  // [3][ntot]: FP64 force
+  auto Q = [&](int k, int c) -> float& {
+    if constexpr (LEAN) return l32[(0 * 3 + c) * N + base + tid + k * nthr];
+    else return q32[k][c];
+  };
+  auto Dl = [&](int k, int c) -> float& {
+    if constexpr (LEAN) return l32[(1 * 3 + c) * N + base + tid + k * nthr];
+    else return d32[k][c];
+  };
+  auto V = [&](int k, int c) -> float& {
+    if constexpr (LEAN) return l32[(2 * 3 + c) * N + base + tid + k * nthr];
+    else return v32[k][c];
+  };
+  auto FR = [&](int k, int c) -> float& {
+    if constexpr (LEAN) return l32[(3 * 3 + c) * N + base + tid + k * nthr];
+    else return fr32[k][c];
+  };
+  auto FU = [&](int k, int c) -> float& {
+    if constexpr (LEAN) return l32[(4 * 3 + c) * N + base + tid + k * nthr];
+    else return Fu[k][c];
+  };
+  auto FD = [&](int k, int c) -> double& {
+    if constexpr (LEAN) return l64[c * N + base + tid + k * nthr];
+    else return F[k][c];
+  };
+  auto pub32 = [&](int k) {  // publish the FP32 view of the record of atom slot k
+    const int li = tid + k * nthr;
+    float qq[3], dq[3];
+#pragma unroll
+    for (int c = 0; c < D; c++) {
+      qq[c] = Q(k, c);
+      dq[c] = Dl(k, c);
+    }
+    store_pub32<D>(&mine[li], qq, dq);
+    if (GREC) store_pub32<D>(&pubg[base + li], qq, dq);
+  };
 #pragma unroll
   for (int k = 0; k < APT; k++) {
     int li = tid + k * nthr;
     ty[k] = 0;
+    if (!LEAN || li < cnt) {
 #pragma unroll
-    for (int c = 0; c < 3; c++) q32[k][c] = d32[k][c] = v32[k][c] = fr32[k][c] = 0.0f;
+      for (int c = 0; c < 3; c++) Q(k, c) = Dl(k, c) = V(k, c) = FR(k, c) = FU(k, c) = 0.0f;
+    }
     if (li < cnt) {
       int64_t gi = base + li;
       ty[k] = A.type[gi];
       if (MIXED && phase == 1)
-        for (int c = 0; c < D; c++) v32[k][c] = (float)A.v[c * N + gi];
+        for (int c = 0; c < D; c++) V(k, c) = (float)A.v[c * N + gi];
       if (LSM) {
         const int nn = A.nnb[gi];
         const uint32_t* row = A.nb + g.nb_off + lo + li;
@@ -315,6 +382,16 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
     cell_origin<D>(H, g.nc, A.cell[gi], o);
     double* q = mine[li].q64;
     for (int c = 0; c < D; c++) q[c] = A.x[c * N + gi] - o[c];
+    if (GREC)
+      for (int c = 0; c < D; c++) pubg[gi].q64[c] = q[c];
+  };
+  // record of a neighbour (owner CTA, slot) for the force phase
+  auto nbrec = [&](uint32_t ent) -> const Pub<D>* {
+    const int ow = nb_owner(ent), sl = nb_slot(ent);
+    if (MEM == 2) return pub + ow * npc + sl;
+    if (ow == rank) return mine + sl;
+    if (GREC) return pubg + (g.off + (int64_t)ow * npc + sl);
+    return rpub[ow] + sl;
   };
   // MEM 2: copy the records of the other CTAs that own neighbours (16-byte words)
   auto stage = [&]() {
@@ -565,8 +642,8 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         for (int c = 0; c < D; c++) {
           A.v[c * N + gi] = 0.0;
           A.xs[c * N + gi] = A.x[c * N + gi];
-          v32[k][c] = 0.0f;
-          d32[k][c] = 0.0f;
+          V(k, c) = 0.0f;
+          Dl(k, c) = 0.0f;
         }
       }
       if (affine) H[1] = fma(dgam, H[D + 1], H[1]);
@@ -599,14 +676,14 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
 #pragma unroll
     for (int m = 0; m < kNumRed; m++) r[m] = 0.0;
     float rf[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // DEV: fmax^2, P, |F|^2, |v|^2, max|delta|^2
-    double F[APT][3];  // FP64 mode / FP64 evaluations
-    float Fu[APT][3];  // mixed: force used by the FP32 update
 #pragma unroll
     for (int k = 0; k < APT; k++) {
+      if constexpr (!LEAN) {
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        F[k][c] = 0.0;
-        Fu[k][c] = 0.0f;
+        for (int c = 0; c < 3; c++) {
+          F[k][c] = 0.0;
+          Fu[k][c] = 0.0f;
+        }
       }
       int li = tid + k * nthr;
       if (li >= cnt) continue;
@@ -615,27 +692,28 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
       const int nn = A.nnb[gi];
       const int ti = ty[k];
       if (mode == kModeEval64) {
-        double qi[3], e = 0.0, w = 0.0;
+        double qi[3], e = 0.0, w = 0.0, Fk[3] = {0.0, 0.0, 0.0};
         load_pub64<D>(&mine[li], qi);
 #pragma unroll 4
         for (int j = 0; j < nn; j++) {
-          uint32_t ent = LSM ? lst[j * lstride + li] : __ldg(row + (int64_t)j * n);
+          uint32_t ent = LSM ? lst[j * lstride + li] : __ldcs(row + (int64_t)j * n);
           double qj[3], d[3];
-          load_pub64<D>(MEM == 2 ? pub + nb_owner(ent) * npc + nb_slot(ent)
-                                 : rpub[nb_owner(ent)] + nb_slot(ent), qj);
+          load_pub64<D>(nbrec(ent), qj);
           const double* of = off64 + 3 * nb_code(ent);
 #pragma unroll
           for (int c = 0; c < D; c++) d[c] = (qj[c] - qi[c]) + of[c];
-          pair64<D>(coef[ti * A.nt + nb_type(ent)], d, F[k], want_e, e, w);
+          pair64<D>(coef[ti * A.nt + nb_type(ent)], d, Fk, want_e, e, w);
         }
+#pragma unroll
+        for (int c = 0; c < D; c++) FD(k, c) = Fk[c];
         r[6] += e;
         r[7] += w;
         double f2 = 0.0, pv = 0.0, v2 = 0.0, u2 = 0.0;
 #pragma unroll
         for (int c = 0; c < D; c++) {
-          double vc = (MIXED && !v64) ? (double)v32[k][c] : A.v[c * N + gi];
-          f2 = fma(F[k][c], F[k][c], f2);
-          pv = fma(F[k][c], vc, pv);
+          double vc = (MIXED && !v64) ? (double)V(k, c) : A.v[c * N + gi];
+          f2 = fma(Fk[c], Fk[c], f2);
+          pv = fma(Fk[c], vc, pv);
           v2 = fma(vc, vc, v2);
           double u = A.x[c * N + gi] - A.xb[c * N + gi];
           u2 = fma(u, u, u2);
@@ -643,9 +721,9 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         if (MIXED) {
 #pragma unroll
           for (int c = 0; c < D; c++) {
-            fr32[k][c] = (float)F[k][c];
-            Fu[k][c] = fr32[k][c];
-            q32[k][c] = (float)qi[c];
+            FR(k, c) = (float)Fk[c];
+            FU(k, c) = (float)Fk[c];
+            Q(k, c) = (float)qi[c];
           }
         }
         r[0] = nmax(r[0], f2);
@@ -656,28 +734,34 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
       } else {
         float qi[3], di[3], f[3] = {0.f, 0.f, 0.f};
         load_pub32<D>(&mine[li], qi, di);
+        // the two species rows of this atom in registers (A.nt <= 2)
+        const Coef32 c0 = coef32(coef[ti * A.nt]);
+        const Coef32 c1 = A.nt > 1 ? coef32(coef[ti * A.nt + 1]) : c0;
 #pragma unroll 4
         for (int j = 0; j < nn; j++) {
-          uint32_t ent = LSM ? lst[j * lstride + li] : __ldg(row + (int64_t)j * n);
+          uint32_t ent = LSM ? lst[j * lstride + li] : __ldcs(row + (int64_t)j * n);
           float qj[3], dj[3], d0[3], e[3];
-          load_pub32<D>(MEM == 2 ? pub + nb_owner(ent) * npc + nb_slot(ent)
-                                 : rpub[nb_owner(ent)] + nb_slot(ent), qj, dj);
-          const float* of = off32 + 3 * nb_code(ent);
+          load_pub32<D>(nbrec(ent), qj, dj);
+          const float* of = off32l + 3 * 32 * nb_code(ent) + lane;
 #pragma unroll
           for (int c = 0; c < D; c++) {
-            d0[c] = (qj[c] - qi[c]) + of[c];
+            d0[c] = (qj[c] - qi[c]) + of[c * 32];
             e[c] = dj[c] - di[c];
           }
-          pair_dev<D>(coef[ti * A.nt + nb_type(ent)], d0, e, f);
+          const int tj = nb_type(ent);
+          const Coef32 cj = A.nt <= 2 ? (tj ? c1 : c0) : coef32(coef[ti * A.nt + tj]);
+          pair_dev<D>(cj, d0, e, f);
         }
         float f2 = 0.f, pv = 0.f, v2 = 0.f, dd = 0.f;
 #pragma unroll
         for (int c = 0; c < D; c++) {
-          Fu[k][c] = fr32[k][c] + f[c];
-          f2 = fmaf(Fu[k][c], Fu[k][c], f2);
-          pv = fmaf(Fu[k][c], v32[k][c], pv);
-          v2 = fmaf(v32[k][c], v32[k][c], v2);
-          dd = fmaf(d32[k][c], d32[k][c], dd);
+          const float fu = FR(k, c) + f[c];
+          const float vk = V(k, c);
+          FU(k, c) = fu;
+          f2 = fmaf(fu, fu, f2);
+          pv = fmaf(fu, vk, pv);
+          v2 = fmaf(vk, vk, v2);
+          dd = fmaf(di[c], di[c], dd);  // the published displacement
         }
         rf[0] = nmaxf(rf[0], f2);
         rf[1] += pv;
@@ -960,10 +1044,11 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
           double sv[3], mx = 0.0;
 #pragma unroll
           for (int cc = 0; cc < D; cc++) {
-            double vc = c.reset ? 0.0 : (v64 ? A.v[cc * N + gv] : (double)v32[k][cc]);
-            vc = fma(c.keep, fma(c.dt, F[k][cc], vc), c.ratio * F[k][cc]);
+            double vc = c.reset ? 0.0 : (v64 ? A.v[cc * N + gv] : (double)V(k, cc));
+            const double fk = FD(k, cc);
+            vc = fma(c.keep, fma(c.dt, fk, vc), c.ratio * fk);
             A.v[cc * N + gv] = vc;
-            v32[k][cc] = (float)vc;  // used only once |v|^2 < kBigV2
+            V(k, cc) = (float)vc;  // used only once |v|^2 < kBigV2
             sv[cc] = c.dt * vc;
             mx = fmax(mx, fabs(sv[cc]));
           }
@@ -976,14 +1061,14 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
             if (len > fp.max_step) scale = fp.max_step / len;
           }
 #pragma unroll
-          for (int cc = 0; cc < D; cc++) d32[k][cc] = (float)((double)d32[k][cc] + scale * sv[cc]);
+          for (int cc = 0; cc < D; cc++) Dl(k, cc) = (float)((double)Dl(k, cc) + scale * sv[cc]);
           if (c.mode == kModeDev) {
-            store_pub32<D>(&mine[li], q32[k], d32[k]);
+            pub32(k);
           } else {  // the next evaluation is FP64: fold delta into x and publish it
             int64_t gi = base + li;
             for (int cc = 0; cc < D; cc++) {
-              A.x[cc * N + gi] += (double)d32[k][cc];
-              d32[k][cc] = 0.0f;
+              A.x[cc * N + gi] += (double)Dl(k, cc);
+              Dl(k, cc) = 0.0f;
             }
             publish64(k);
           }
@@ -1000,9 +1085,10 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
           float sv[3], mx = 0.0f;
 #pragma unroll
           for (int cc = 0; cc < D; cc++) {
-            float vc = c.reset ? 0.0f : v32[k][cc];
-            vc = fmaf(kf, fmaf(dtf, Fu[k][cc], vc), rf * Fu[k][cc]);
-            v32[k][cc] = vc;
+            float vc = c.reset ? 0.0f : V(k, cc);
+            const float fu = FU(k, cc);
+            vc = fmaf(kf, fmaf(dtf, fu, vc), rf * fu);
+            V(k, cc) = vc;
             sv[cc] = dtf * vc;
             mx = fmaxf(mx, fabsf(sv[cc]));
           }
@@ -1015,14 +1101,14 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
             if (len > ms) scale = ms / len;
           }
 #pragma unroll
-          for (int cc = 0; cc < D; cc++) d32[k][cc] = fmaf(scale, sv[cc], d32[k][cc]);
+          for (int cc = 0; cc < D; cc++) Dl(k, cc) = fmaf(scale, sv[cc], Dl(k, cc));
           if (c.mode == kModeDev) {
-            store_pub32<D>(&mine[li], q32[k], d32[k]);
+            pub32(k);
           } else {  // the next evaluation is FP64: fold delta into x and publish it
             int64_t gi = base + li;
             for (int cc = 0; cc < D; cc++) {
-              A.x[cc * N + gi] += (double)d32[k][cc];
-              d32[k][cc] = 0.0f;
+              A.x[cc * N + gi] += (double)Dl(k, cc);
+              Dl(k, cc) = 0.0f;
             }
             publish64(k);
           }
@@ -1038,7 +1124,8 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
 #pragma unroll
           for (int cc = 0; cc < D; cc++) {
             double vc = c.reset ? 0.0 : A.v[cc * N + gi];
-            vc = fma(keep, fma(cdt, F[k][cc], vc), ratio * F[k][cc]);
+            const double fk = FD(k, cc);
+            vc = fma(keep, fma(cdt, fk, vc), ratio * fk);
             A.v[cc * N + gi] = vc;
             s[cc] = cdt * vc;
             mx = fmax(mx, fabs(s[cc]));
@@ -1064,8 +1151,8 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         if (li >= cnt) continue;
         int64_t gi = base + li;
         for (int cc = 0; cc < D; cc++) {
-          A.x[cc * N + gi] += (double)d32[k][cc];
-          d32[k][cc] = 0.0f;
+          A.x[cc * N + gi] += (double)Dl(k, cc);
+          Dl(k, cc) = 0.0f;
         }
         publish64(k);
       }
@@ -1080,14 +1167,15 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         if (li >= cnt) continue;
         int64_t gi = base + li;
         for (int c = 0; c < D; c++) {
-          A.x[c * N + gi] += (double)d32[k][c];
-          d32[k][c] = 0.0f;
+          A.x[c * N + gi] += (double)Dl(k, c);
+          Dl(k, c) = 0.0f;
         }
       }
     }
     if (status == kStatusRebuild && A.inkernel_rebuild) {
       // rebuild the lists here and resume the same FIRE state
       if (rebuild_lists()) {
+        kreb++;
         tilt_b = H[1];
         wmaxf = 0.0f;
         status = kStatusRunning;
@@ -1176,7 +1264,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
       int li = tid + k * nthr;
       if (li >= cnt) continue;
       int64_t gi = base + li;
-      for (int c = 0; c < D; c++) A.v[c * N + gi] = (double)v32[k][c];
+      for (int c = 0; c < D; c++) A.v[c * N + gi] = (double)V(k, c);
     }
   }
   if (rank == 0 && tid == 0) {
@@ -1189,6 +1277,7 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
     st->acc_iters = acc_it;
     st->acc64 = acc64;
     st->acc32 = acc32;
+    st->kreb = kreb;
     st->status = status;
     st->fmax = fmx;
     st->step = step;

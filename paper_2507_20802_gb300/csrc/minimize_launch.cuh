@@ -6,7 +6,7 @@ namespace aqs {
 
 inline size_t smem_fixed(int nt) {
   return sizeof(double) * (kNumRed * 33 + 27 * 3) + sizeof(float) * (27 * 3 + 3) +
-         sizeof(PairCoef) * nt * nt + 64;
+         sizeof(float) * kOffLane + sizeof(PairCoef) * nt * nt + 64;
 }
 
 inline size_t pub_size(int dim) { return dim == 2 ? sizeof(Pub<2>) : sizeof(Pub<3>); }
@@ -18,7 +18,10 @@ inline size_t minimize_smem_bytes_impl(int dim, int npc, int nrep, int nt, int c
 
 constexpr size_t kSmemLimit = 220 * 1024;
 
-inline int choose_mem(int dim, int npc, int nrep, int nt, int cap) {
+inline int choose_mem(int dim, int npc, int nrep, int nt, int cap, int want = -1) {
+  if (want >= 0 && want < kNumStaging &&
+      minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, want) <= kSmemLimit)
+    return want;
   if (minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, 2) <= kSmemLimit) return 2;
   if (minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, 1) <= kSmemLimit) return 1;
   return 0;
@@ -75,6 +78,7 @@ template <int D, bool MIXED>
 cudaError_t run_mem(int mem, const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
                            cudaStream_t s, int* max_clusters) {
   switch (mem) {
+    case 3: return run_apt<D, MIXED, 3>(a, n_clusters, C, npc, smem, s, max_clusters);
     case 2: return run_apt<D, MIXED, 2>(a, n_clusters, C, npc, smem, s, max_clusters);
     case 1: return run_apt<D, MIXED, 1>(a, n_clusters, C, npc, smem, s, max_clusters);
     default: return run_apt<D, MIXED, 0>(a, n_clusters, C, npc, smem, s, max_clusters);

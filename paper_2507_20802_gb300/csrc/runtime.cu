@@ -66,7 +66,11 @@ struct aqs_system {
   // choices made so far, keyed by (replicas in flight, largest N)
   int64_t tune_iters = 0;
   bool tuning = false;
-  std::map<std::pair<int, int64_t>, int> tuned;
+  std::map<std::pair<int, int64_t>, std::pair<int, int>> tuned;  // -> (C, staging)
+  // staging mode of the minimiser launches (-1: automatic); staging_user marks
+  // a mode the caller fixed, which the tuner leaves alone
+  int staging = -1;
+  bool staging_user = false;
   aqs_potential pot{};
   double skin = 0.3, rcmax = 0.0, rlist = 0.0;
   cudaStream_t stream = nullptr;
@@ -108,6 +112,9 @@ struct aqs_system {
   double* d_partial = nullptr;
   int64_t* d_i64 = nullptr;  // small scratch (copy offsets)
   double* d_shift = nullptr;
+  double* pubg = nullptr;  // [ntot] position records (16 B in 2D, 32 B in 3D)
+  float* lean32 = nullptr;  // per-atom minimiser state of large-CTA launches
+  double* lean64 = nullptr;
   // per-step job records and first-step snapshots
   double* d_rec = nullptr;
   int64_t rec_cap = 0;
@@ -445,6 +452,9 @@ MinArgs min_args(aqs_system* s, const aqs_fire_params* f) {
   a.cellatoms = s->itmp;  // host rebuilds use it only between launches
   a.cap = s->cap;
   a.inkernel_rebuild = 1;
+  a.pubg = s->pubg;
+  a.lean32 = s->lean32;
+  a.lean64 = s->lean64;
   for (int k = 0; k < AQS_MAX_TYPES * AQS_MAX_TYPES; k++) a.rl2f[k] = s->rl2f[k];
   return a;
 }
@@ -502,7 +512,8 @@ aqs_status ensure_records(aqs_system* s, int64_t nsteps, bool snap) {
 }
 
 aqs_status tune_clusters(aqs_system* s, const aqs_fire_params* f, const std::vector<uint8_t>& mask,
-                         int64_t iters, int* best, double* ms_per_iter);
+                         int64_t iters, int* best, int* best_staging, double* ms_per_iter,
+                         double* ms_per_staging);
 aqs_status apply_cluster(aqs_system* s, const std::vector<int>& reps, int C);
 
 // Runs the jobs of the replicas with jobs[r].nsteps > 0 to completion in
@@ -524,11 +535,12 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
       const auto key = std::make_pair((int)reps.size(), nmax);
       auto it = s->tuned.find(key);
       if (it == s->tuned.end()) {
-        int best = 0;
-        AQS_TRY(tune_clusters(s, f, mask, s->tune_iters, &best, nullptr));
-        s->tuned[key] = best;
+        int best = 0, mode = -1;
+        AQS_TRY(tune_clusters(s, f, mask, s->tune_iters, &best, &mode, nullptr, nullptr));
+        s->tuned[key] = std::make_pair(best, mode);
       } else {
-        AQS_TRY(apply_cluster(s, reps, it->second));
+        if (!s->staging_user) s->staging = it->second.second;
+        AQS_TRY(apply_cluster(s, reps, it->second.first));
       }
     }
   }
@@ -554,6 +566,8 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
   AQS_TRY(ensure_records(s, maxsteps, snap));
   AQS_TRY(upload_state(s));
   std::vector<int64_t> rebuilds(s->R, 0);
+  std::vector<int> kreb0(s->R);
+  for (int r = 0; r < s->R; r++) kreb0[r] = s->st[r].kreb;
   std::vector<int> order_work;
   for (int64_t pass = 0; pass < 100000000 && !todo.empty(); pass++) {
     std::vector<int> Cs;
@@ -570,6 +584,15 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
     }
     CUDA_TRY(cudaMemcpyAsync(s->d_work, order_work.data(), sizeof(int) * order_work.size(),
                              cudaMemcpyHostToDevice, s->stream));
+    if (!s->lean32) {
+      bool lean = false;
+      for (int r : todo)
+        lean = lean || minimize_is_lean(s->dim, minimize_atoms_per_thread(s->geom[r].npc));
+      if (lean) {
+        AQS_TRY(alloc_arr(s, &s->lean32, (size_t)15 * s->ntot));
+        AQS_TRY(alloc_arr(s, &s->lean64, (size_t)3 * s->ntot));
+      }
+    }
     MinArgs a = min_args(s, f);
     a.warm_u = warm_u;
     const bool timing = g_timing.load() != 0;
@@ -599,7 +622,7 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
         CUDA_TRY(cudaStreamWaitEvent(st, s->aux_ev[4], 0));
       }
       CUDA_TRY(launch_minimize(s->dim, s->prec == AQS_MIXED, a, groups[gi].second, C, npc, nrep,
-                               s->cap, st));
+                               s->cap, st, s->staging));
       if (multi) CUDA_TRY(cudaEventRecord(s->aux_ev[gi % 4], st));
       if (multi && (gi % 4 == 3 || gi + 1 == groups.size()))
         for (size_t k = 0; k <= gi % 4; k++) CUDA_TRY(cudaStreamWaitEvent(s->stream, s->aux_ev[k], 0));
@@ -620,6 +643,7 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
         g_stats.pairs32 += d32 * s->nnb_sum[r];
         g_stats.pairs64 += d64 * s->nnb_sum[r];
         g_stats.atom_iters += dit * s->n[r];
+        g_stats.rebuilds += s->st[r].kreb - before[r].kreb;
       }
     }
     std::vector<uint8_t> flags(s->R, 0);
@@ -656,6 +680,7 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
                              cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     out->rebuilds = rebuilds;
+    for (int r = 0; r < s->R; r++) out->rebuilds[r] += s->st[r].kreb - kreb0[r];
   }
   aqs_status first = AQS_OK;
   for (int r = 0; r < s->R; r++) {
@@ -750,6 +775,7 @@ aqs_status alloc_system(aqs_system* s) {
   AQS_TRY(alloc_arr(s, &s->d_i64, 4 * std::max(s->R, 64)));
   AQS_TRY(alloc_arr(s, &s->d_shift, std::max(s->R, 64)));
   AQS_TRY(alloc_arr(s, &s->d_nnbsum, s->R));
+  AQS_TRY(alloc_arr(s, &s->pubg, (size_t)N * (D == 2 ? 2 : 4)));
   CUDA_TRY(cudaEventCreate(&s->ev0));
   CUDA_TRY(cudaEventCreate(&s->ev1));
   CUDA_TRY(cudaMemsetAsync(s->v, 0, sizeof(double) * D * N, s->stream));
@@ -905,6 +931,8 @@ aqs_status ensure_chains(aqs_system* s, int src, int P) {
     return fail(AQS_ERR_OOM, "chain snapshot allocation failed");
   }
   c->tune_iters = s->tune_iters;
+  c->staging = s->staging_user ? s->staging : -1;
+  c->staging_user = s->staging_user;
   s->chains = c;
   return AQS_OK;
 }
@@ -1390,15 +1418,16 @@ int aqs_cluster_size(const aqs_system* s, int r) {
 }
 
 aqs_status aqs_autotune_clusters(aqs_system* s, const aqs_fire_params* f, int64_t iters,
-                                 const uint8_t* mask, int* best_cluster, double* ms_per_iter) {
+                                 const uint8_t* mask, int* best_cluster, int* best_staging,
+                                 double* ms_per_iter, double* ms_per_staging) {
   if (!s || !f || iters <= 0) return fail(AQS_ERR_INVALID_ARG, "autotune: bad arguments");
   if (s->C_override > 0)
     return fail(AQS_ERR_INVALID_ARG, "autotune: the system has an explicit cluster size");
   std::vector<uint8_t> m(s->R, 1);
   if (mask)
     for (int r = 0; r < s->R; r++) m[r] = mask[r] ? 1 : 0;
-  int best = 0;
-  AQS_TRY(tune_clusters(s, f, m, iters, &best, ms_per_iter));
+  int best = 0, mode = -1;
+  AQS_TRY(tune_clusters(s, f, m, iters, &best, &mode, ms_per_iter, ms_per_staging));
   int64_t nmax = 0;
   int cnt = 0;
   for (int r = 0; r < s->R; r++)
@@ -1406,9 +1435,28 @@ aqs_status aqs_autotune_clusters(aqs_system* s, const aqs_fire_params* f, int64_
       nmax = std::max(nmax, s->n[r]);
       cnt++;
     }
-  if (best > 0) s->tuned[std::make_pair(cnt, nmax)] = best;
+  if (best > 0) s->tuned[std::make_pair(cnt, nmax)] = std::make_pair(best, mode);
   if (best_cluster) *best_cluster = best;
+  if (best_staging) *best_staging = mode;
   return AQS_OK;
+}
+
+aqs_status aqs_set_staging(aqs_system* s, int mode) {
+  if (!s || mode < -1 || mode >= kNumStaging)
+    return fail(AQS_ERR_INVALID_ARG, "set_staging: mode must be -1 or 0..%d", kNumStaging - 1);
+  s->staging = mode;
+  s->staging_user = mode >= 0;
+  if (s->chains) {
+    s->chains->staging = mode;
+    s->chains->staging_user = mode >= 0;
+  }
+  return AQS_OK;
+}
+
+int aqs_staging(const aqs_system* s, int replica) {
+  if (!s || replica < 0 || replica >= s->R) return -1;
+  const RepGeom& g = s->geom[replica];
+  return minimize_staging(s->dim, g.npc, g.n, s->nt, s->cap, s->staging);
 }
 
 aqs_status aqs_set_autotune(aqs_system* s, int64_t iters) {
@@ -1572,23 +1620,57 @@ bool cluster_feasible(const aqs_system* s, const std::vector<int>& reps, int C) 
     const int64_t npc = (s->n[r] + C - 1) / C;
     if (npc > 4096 || (C > 1 && s->n[r] < 32 * (int64_t)C)) return false;
     if (minimize_max_active_clusters(s->dim, s->prec == AQS_MIXED, C, (int)npc, (int)s->n[r],
-                                     s->nt, s->cap) <= 0)
+                                     s->nt, s->cap, s->staging) <= 0)
       return false;
   }
   return true;
 }
 
+// Times one candidate (cluster size C, the system's current staging mode) on
+// the masked replicas: an untimed short run, then `ft` timed; the
+// configuration is restored after each run.
+aqs_status time_candidate(aqs_system* s, const aqs_fire_params& ft, const aqs_fire_params& fw,
+                          const std::vector<uint8_t>& mask, const std::vector<int>& reps,
+                          const std::vector<double>& tilt, int C, double* ms) {
+  s->C_override = C;  // no cluster growth while a candidate is timed
+  AQS_TRY(apply_cluster(s, reps, C));
+  aqs_status st = minimize_impl(s, &fw, mask, nullptr);
+  if (st != AQS_OK && st != AQS_ERR_NOT_CONVERGED) return st;
+  AQS_TRY(restore_positions(s, mask, tilt));
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return fail(AQS_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+  const auto t0 = std::chrono::steady_clock::now();
+  st = minimize_impl(s, &ft, mask, nullptr);
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return fail(AQS_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+  const auto t1 = std::chrono::steady_clock::now();
+  if (st != AQS_OK && st != AQS_ERR_NOT_CONVERGED) return st;
+  int64_t it = 1;
+  for (int r : reps) it = std::max<int64_t>(it, s->st[r].iters);
+  *ms = std::chrono::duration<double, std::milli>(t1 - t0).count() / (double)it;
+  return restore_positions(s, mask, tilt);
+}
+
 // Times `iters` FIRE iterations (convergence test off) of the masked replicas
-// for every feasible cluster size and keeps the fastest; the configuration
-// and the host-side minimiser state are restored after every candidate.
+// for every feasible cluster size (automatic staging), then every staging mode
+// that fits at the fastest size, and keeps the fastest pair; the
+// configuration and the host-side minimiser state are restored afterwards.
 aqs_status tune_clusters(aqs_system* s, const aqs_fire_params* f, const std::vector<uint8_t>& mask,
-                         int64_t iters, int* best, double* ms_per_iter) {
+                         int64_t iters, int* best, int* best_staging, double* ms_per_iter,
+                         double* ms_per_staging) {
   std::vector<int> reps;
+  int64_t nmax = 0;
   for (int r = 0; r < s->R; r++)
-    if (mask[r]) reps.push_back(r);
+    if (mask[r]) {
+      reps.push_back(r);
+      nmax = std::max(nmax, s->n[r]);
+    }
   if (ms_per_iter)
     for (int c = 0; c <= kMaxCluster; c++) ms_per_iter[c] = -1.0;
+  if (ms_per_staging)
+    for (int m = 0; m < kNumStaging; m++) ms_per_staging[m] = -1.0;
   if (best) *best = 0;
+  if (best_staging) *best_staging = s->staging;
   if (reps.empty() || iters <= 0) return AQS_OK;
   if (!s->d_save) AQS_TRY(alloc_arr(s, &s->d_save, (size_t)s->ntot * s->dim));
   AQS_TRY(save_positions(s));
@@ -1604,49 +1686,40 @@ aqs_status tune_clusters(aqs_system* s, const aqs_fire_params* f, const std::vec
   ft.max_iter = iters;
   aqs_fire_params fw = ft;
   fw.max_iter = std::min<int64_t>(iters, 32);
-  const int saved_override = s->C_override;
+  const int saved_override = s->C_override, saved_staging = s->staging;
   s->tuning = true;
-  int bestC = 0;
+  if (!s->staging_user) s->staging = -1;
+  int bestC = 0, bestM = s->staging;
   double bestT = 1e300;
   aqs_status err = AQS_OK;
   for (int C = 1; C <= kMaxCluster && err == AQS_OK; C++) {
     if (!cluster_feasible(s, reps, C)) continue;
-    s->C_override = C;  // no cluster growth while a candidate is timed
-    if ((err = apply_cluster(s, reps, C)) != AQS_OK) break;
-    // untimed first launch of this kernel instance
-    aqs_status st = minimize_impl(s, &fw, mask, nullptr);
-    if (st != AQS_OK && st != AQS_ERR_NOT_CONVERGED) {
-      err = st;
-      break;
-    }
-    if ((err = restore_positions(s, mask, tilt)) != AQS_OK) break;
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
-      err = fail(AQS_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
-      break;
-    }
-    const auto t0 = std::chrono::steady_clock::now();
-    st = minimize_impl(s, &ft, mask, nullptr);
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
-      err = fail(AQS_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
-      break;
-    }
-    const auto t1 = std::chrono::steady_clock::now();
-    if (st != AQS_OK && st != AQS_ERR_NOT_CONVERGED) {
-      err = st;
-      break;
-    }
-    int64_t it = 1;
-    for (int r : reps) it = std::max<int64_t>(it, s->st[r].iters);
-    const double ms = std::chrono::duration<double, std::milli>(t1 - t0).count() / (double)it;
+    double ms = 0.0;
+    if ((err = time_candidate(s, ft, fw, mask, reps, tilt, C, &ms)) != AQS_OK) break;
     if (ms_per_iter) ms_per_iter[C] = ms;
     if (ms < bestT) {
       bestT = ms;
       bestC = C;
     }
-    err = restore_positions(s, mask, tilt);
+  }
+  if (err == AQS_OK && bestC > 0 && !s->staging_user) {
+    const int npc = (int)((nmax + bestC - 1) / bestC);
+    for (int m = 0; m < kNumStaging && err == AQS_OK; m++) {
+      if (minimize_staging(s->dim, npc, (int)nmax, s->nt, s->cap, m) != m) continue;
+      s->staging = m;
+      if (!cluster_feasible(s, reps, bestC)) continue;
+      double ms = 0.0;
+      if ((err = time_candidate(s, ft, fw, mask, reps, tilt, bestC, &ms)) != AQS_OK) break;
+      if (ms_per_staging) ms_per_staging[m] = ms;
+      if (ms < bestT) {
+        bestT = ms;
+        bestM = m;
+      }
+    }
   }
   s->tuning = false;
   s->C_override = saved_override;
+  s->staging = err == AQS_OK ? bestM : saved_staging;
   for (int r : reps) {
     const int C = (err == AQS_OK && bestC > 0) ? bestC : c0[r];
     s->geom[r].C = C;
@@ -1657,6 +1730,7 @@ aqs_status tune_clusters(aqs_system* s, const aqs_fire_params* f, const std::vec
   if (err != AQS_OK) return err;
   if (rs != AQS_OK) return rs;
   if (best) *best = bestC;
+  if (best_staging) *best_staging = s->staging;
   return AQS_OK;
 }
 

@@ -64,9 +64,9 @@ def test_struct_layouts_match_header():
 #include <stdio.h>
 #include "aqs.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(aqs_potential), sizeof(aqs_system_desc),
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(aqs_potential), sizeof(aqs_system_desc),
          sizeof(aqs_fire_params), sizeof(aqs_min_result), sizeof(aqs_parallel_params),
-         sizeof(aqs_parallel_result));
+         sizeof(aqs_parallel_result), sizeof(aqs_kernel_stats));
   return 0;
 }
 '''
@@ -79,5 +79,6 @@ int main(void) {
                                                 check=True).stdout.split()]
     mine = [ctypes.sizeof(t) for t in (aqs.aqs_potential, aqs.aqs_system_desc,
                                        aqs.aqs_fire_params, aqs.aqs_min_result,
-                                       aqs.aqs_parallel_params, aqs.aqs_parallel_result)]
+                                       aqs.aqs_parallel_params, aqs.aqs_parallel_result,
+                                       aqs.aqs_kernel_stats)]
     assert sizes == mine

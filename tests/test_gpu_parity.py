@@ -293,3 +293,44 @@ def test_uneven_batch_reproduces_single_glass_trajectory(A, syn, glass256):
     for r in range(1, len(sizes)):
         _, F, _ = s.energy_forces(r)
         assert np.sqrt((F * F).sum(1)).max() < 1e-10
+
+
+# ------------------------------------------------------------ large CTAs
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("C", [1, 2])
+def test_lean_launches_match_3d_golden(A, syn, prec, C):
+    """One replica on 1 or 2 CTAs (2048 or 1024 atoms per CTA: 4 or 2 atoms
+    per thread, per-atom state kept in global memory) follows the stored
+    oracle run like the default launch."""
+    g = load_golden("glass_3d_n2048_s0.npz")
+    gold = load_golden("aqs_3d_n2048_s0.npz")
+    P = A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED
+    s = make_system(A, syn, g["x"], g["types"], g["H"], P, cluster_size=C)
+    assert s.cluster_size(0) == C
+    out = s.run_sequential(float(gold["dgamma"]), int(gold["n_steps"]))
+    rel = 1e-9 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(out["E"][:, 0], gold["E"], rtol=rel)
+    np.testing.assert_allclose(out["tau"][:, 0], gold["tau"], rtol=1e-6, atol=1e-7)
+    assert mi_disp(s.positions(), gold["x"], gold["H"]) < 1e-6
+    np.testing.assert_allclose(out["D"][:, 0], gold["D"], rtol=1e-3)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_lean_launch_2d_matches_register_launch(A, syn, prec):
+    """2D glass of 2048 atoms on one CTA (4 atoms per thread, lean) against the
+    same glass on 16 CTAs (1 atom per thread), through shear steps with
+    plastic events: same minima, energies and events."""
+    x, t, H = syn.random_glass_start(2048, 2, seed=5)
+    q = make_system(A, syn, x, t, H, A.AQS_FP64)
+    q.minimize(A.fire_params(max_iter=1_000_000))
+    xq, Hq = q.positions(), q.box()
+    P = A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED
+    runs = []
+    for C in (1, 16):
+        s = make_system(A, syn, xq, t, Hq, P, cluster_size=C)
+        runs.append((s.run_sequential(1e-3, 6), s))
+    (a, sa), (b, sb) = runs
+    rel = 1e-9 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(a["E"], b["E"], rtol=rel)
+    assert np.array_equal(a["D"] > EV_THR, b["D"] > EV_THR)
+    assert mi_disp(sa.positions(), sb.positions(), sb.box()) < 1e-6
