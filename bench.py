@@ -245,11 +245,13 @@ def run_batch64(args):
 
 
 def run_glass3d(args):
-    """3D binary LJ glass (80:20, N = 65536, density 1.2): the 32 level-I
-    predictions of Algorithm 1 (shear i * 20 * 5e-5 of the quenched glass) as
-    32 replicas, minimised together for a bounded number of FIRE iterations.
-    value = FIRE iterations / s summed over the replicas; the roofline reports
-    the force kernel's streamed list and position bytes against HBM."""
+    """3D binary LJ glass (80:20, N = 65536, density 1.2), the level-II fine
+    steps of Algorithm 1: replica i is the quenched glass after (i + 1) fine
+    shear steps of 5e-5, and the replicas are minimised together for a bounded
+    number of FIRE iterations (the regime where AQS spends its iterations:
+    small displacements from a converged state).  value = FIRE iterations / s
+    summed over the replicas; the roofline reports the force kernel's streamed
+    list and position bytes against HBM."""
     import torch
     from paper_2507_20802_gb300 import aqs as A, synthetic as syn
     torch.cuda.set_device(0)
@@ -262,7 +264,7 @@ def run_glass3d(args):
     s.close()
     b = A.System(np.tile(xq, (P, 1)), np.tile(t, P), np.tile(Hq[None], (P, 1, 1)), [n] * P,
                  syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR, precision=A.AQS_MIXED)
-    b.shear(np.arange(P) * K * dg)
+    b.shear((np.arange(P) + 1) * dg)
     nb = b.mean_neighbours(0)
     budget = args.iters3d
     b.minimize(A.fire_params(max_iter=50), check_status=False)  # warm-up
@@ -291,10 +293,11 @@ def run_glass3d(args):
     gbs = algo_bytes / kern_s / 1e9 if kern_s else 0.0
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
-    config = {"workload": "3D binary LJ glass (80:20, rho=1.2), N=65536, %d level-I "
-                          "predictions (K=20, dgamma=5e-5) minimised as one batch for a bounded "
-                          "number of FIRE iterations, mixed precision" % P,
-              "n_atoms": n, "P": P, "K": K, "dgamma": dg, "fire_iterations_budget": budget,
+    config = {"workload": "3D binary LJ glass (80:20, rho=1.2), N=65536: %d replicas, replica i "
+                          "the quenched glass after i+1 fine shear steps of dgamma=5e-5, minimised "
+                          "as one batch for a bounded number of FIRE iterations, mixed precision"
+                          % P,
+              "n_atoms": n, "replicas": P, "dgamma": dg, "fire_iterations_budget": budget,
               "l2": "working set (~%d MB of lists) exceeds L2" % int(4 * nb * n * P / 1e6)}
     _line("FIRE iterations/s (3D, %d x 65536 atoms)" % P, iters / secs, "iterations/s", args,
           1e3 * secs, config,
@@ -320,6 +323,8 @@ def main():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--baseline-steps", type=int, default=2)
     ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d"], default="cfg1")
+    ap.add_argument("--autotune", type=int, default=300,
+                    help="FIRE iterations per autotuner candidate (0: size rule only)")
     ap.add_argument("--quench-iters", type=int, default=400000)
     ap.add_argument("--iters3d", type=int, default=2000)
     ap.add_argument("--replicas3d", type=int, default=32)
@@ -351,6 +356,10 @@ def main():
     g.close()
     s = A.System(xq, t, Hq[None], [N_ATOMS], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
                  precision=A.AQS_MIXED)
+    if args.autotune > 0:
+        # the chains tune cluster size and staging during the first (untimed)
+        # warm-up pass
+        s.set_autotune(args.autotune)
     fire = A.fire_params()
     n_total = int(round(GAMMA_END / DGAMMA))
     done = 0
@@ -381,7 +390,7 @@ def main():
     launches0 = A.aqs_launch_count()
     gpu_index = int((os.environ.get("CUDA_VISIBLE_DEVICES") or str(local)).split(",")[0]) \
         if (os.environ.get("CUDA_VISIBLE_DEVICES") or "").split(",")[0].isdigit() else local
-    accepted, dev_ms, wall, iters, rej = 0, 0.0, 0.0, [], 0
+    accepted, dev_ms, wall, iters, rej, stopped = 0, 0.0, 0.0, [], 0, 0
     barrier()
     with Clocks(gpu_index) as clk:
         for _ in range(args.steps):
@@ -397,6 +406,7 @@ def main():
             dev_ms += e0.elapsed_time(e1)
             accepted += r["accepted"]
             rej += r["rejections"]
+            stopped += r["chains_stopped"]
             iters.extend(r["iters"].tolist())
     barrier()
     gpu_launches = A.aqs_launch_count() - launches0
@@ -494,6 +504,7 @@ def main():
                 "cpu_baseline": cpu,
                 "fp64_sequential_gpu_baseline": base,
                 "detail": {"accepted_steps": int(total_steps), "rejections": rej,
+                           "chains_stopped_early": stopped, "autotune_iters": args.autotune,
                            "wall_s": wall, "fire_iters_per_step": mean_iters,
                            "fp32_evals": st["evals32"], "fp64_evals": st["evals64"],
                            "rebuilds_in_kernel": st["rebuilds"],

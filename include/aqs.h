@@ -175,6 +175,11 @@ typedef struct {
   int64_t max_iterations; /* while-loop passes in this call; <= 0: until n_steps */
   int warm_start;         /* 1: start each fine minimisation from the learned
                              prediction (see aqs_warm_*); 0: plain affine start */
+  int run_discarded;      /* 0 (default): a chain stops as soon as a failed
+                             equality test of an earlier or the same chain
+                             index shows that its result will be discarded;
+                             1: every chain runs to its end as in the paper.
+                             Results and decisions are identical. */
 } aqs_parallel_params;
 
 typedef struct {
@@ -183,6 +188,7 @@ typedef struct {
   int64_t rejections;       /* passes that ended at a failed equality test */
   int64_t fire_iters_total; /* FIRE iterations of all chains, rejected ones included */
   int64_t evals64_total;    /* FP64 force evaluations of all chains */
+  int64_t chains_stopped;   /* chains stopped early (see run_discarded) */
   /* caller-allocated host arrays indexed by accepted step (nullable each),
    * capacity n_steps: */
   double* energy;

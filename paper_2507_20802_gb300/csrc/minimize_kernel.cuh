@@ -484,6 +484,14 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         mul *= g.nc[c];
       }
       A.cell[gi] = key;
+      // FP32 position relative to the new cell origin, computed once per atom
+      // and read by every candidate test below (the global record array is
+      // free during the rebuild; the records are published again after it)
+      double o[3];
+      cell_origin<D>(H, g.nc, key, o);
+      float qf[3] = {0.f, 0.f, 0.f}, zf[3] = {0.f, 0.f, 0.f};
+      for (int c = 0; c < D; c++) qf[c] = (float)(A.x[c * N + gi] - o[c]);
+      store_pub32<D>(&pubg[gi], qf, zf);
     }
     cl.sync();
     // 2. histogram
@@ -567,10 +575,8 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
       const int il = lo + li;
       const int ci = A.cell[gi];
       int cc[3] = {ci % g.nc[0], (ci / g.nc[0]) % g.nc[1], D == 3 ? ci / (g.nc[0] * g.nc[1]) : 0};
-      double oi[3];
-      cell_origin<D>(H, g.nc, ci, oi);
-      float qi[3];
-      for (int c = 0; c < D; c++) qi[c] = (float)(A.x[c * N + gi] - oi[c]);
+      float qi[3], zi[3];
+      load_pub32<D>(&pubg[gi], qi, zi);
       const int ti = ty[k];
       int m = 0;
       unsigned own = 0u;
@@ -580,17 +586,17 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
         const int ny = (cc[1] + dy + g.nc[1]) % g.nc[1];
         const int nz = D == 3 ? (cc[2] + dz + g.nc[2]) % g.nc[2] : 0;
         const int cj = nx + g.nc[0] * (ny + g.nc[1] * nz);
-        double oj[3];
-        cell_origin<D>(H, g.nc, cj, oj);
         const float* of = off32 + 3 * code;
         const int b = A.cstart[g.cell_off + cj], e = A.cstart[g.cell_off + cj + 1];
         for (int p = b; p < e; p++) {
           const int jl = A.cellatoms[g.off + p];
           if (jl == il) continue;
           const int64_t gj = g.off + jl;
+          float qj[3], zj[3];
+          load_pub32<D>(&pubg[gj], qj, zj);
           float s2 = 0.0f;
           for (int c = 0; c < D; c++) {
-            float d = ((float)(A.x[c * N + gj] - oj[c]) - qi[c]) + of[c];
+            float d = (qj[c] - qi[c]) + of[c];
             s2 = fmaf(d, d, s2);
           }
           const int tj = A.type[gj];

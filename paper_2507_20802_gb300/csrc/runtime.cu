@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstddef>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <string>
 #include <utility>
@@ -516,11 +517,18 @@ aqs_status tune_clusters(aqs_system* s, const aqs_fire_params* f, const std::vec
                          double* ms_per_staging);
 aqs_status apply_cluster(aqs_system* s, const std::vector<int>& reps, int C);
 
+// Called by run_jobs after every pass with the replicas that are still
+// running; it may remove replicas whose results are no longer needed (they
+// are marked in `dropped` and stop without a final status).
+using PassHook = std::function<aqs_status(std::vector<int>& next, std::vector<uint8_t>& dropped)>;
+
 // Runs the jobs of the replicas with jobs[r].nsteps > 0 to completion in
 // persistent launches (one per cluster size and pass); between passes only
 // list rebuilds and budget yields are handled on the host.
 aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<Job>& jobs,
-                    JobOut* out, const float* warm_u = nullptr) {
+                    JobOut* out, const float* warm_u = nullptr, const PassHook* hook = nullptr,
+                    std::vector<uint8_t>* dropped_out = nullptr) {
+  std::vector<uint8_t> dropped(s->R, 0);
   if (s->tune_iters > 0 && s->C_override <= 0 && !s->tuning) {
     std::vector<uint8_t> mask(s->R, 0);
     std::vector<int> reps;
@@ -656,6 +664,11 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
       }
       if (st == kStatusRebuild || st == kStatusRunning) next.push_back(r);
     }
+    if (hook && !next.empty()) {
+      AQS_TRY((*hook)(next, dropped));
+      for (int r = 0; r < s->R; r++)
+        if (dropped[r]) flags[r] = 0;
+    }
     // fewer replicas left: give each a larger cluster (the list is rebuilt
     // for the new owner layout; the FIRE state carries over)
     if (s->C_override <= 0 && !next.empty() && next.size() < todo.size()) {
@@ -683,8 +696,9 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
     for (int r = 0; r < s->R; r++) out->rebuilds[r] += s->st[r].kreb - kreb0[r];
   }
   aqs_status first = AQS_OK;
+  if (dropped_out) *dropped_out = dropped;
   for (int r = 0; r < s->R; r++) {
-    if (jobs[r].nsteps <= 0) continue;
+    if (jobs[r].nsteps <= 0 || dropped[r]) continue;
     const RepState& t = s->st[r];
     if (t.status != AQS_OK && first == AQS_OK) {
       first = (aqs_status)t.status;
@@ -1181,6 +1195,7 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
   aqs_system* c = s->chains;
   out->iterations = out->accepted_steps = out->rejections = 0;
   out->fire_iters_total = out->evals64_total = 0;
+  out->chains_stopped = 0;
   out->n_log = 0;
   std::vector<double> cE((size_t)P * K), cT((size_t)P * K), cD((size_t)P * K);
   std::vector<int64_t> cI((size_t)P * K);
@@ -1210,13 +1225,79 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
       jobs[i].first_noaffine = 1;
       jobs[i].want_snap = i >= 1;
     }
+    // Equality tests (Eq. 20): end of chain i-1 vs F(r^c_iK), the snapshot
+    // of chain i after its first minimisation.  A test is made as soon as
+    // both are available (between persistent-launch passes); once a test i
+    // fails, chains i.. are discarded whatever the earlier tests give, so
+    // unless run_discarded is set they stop there and their SMs go to the
+    // chains that are still needed.  Decisions are the same either way.
+    std::vector<double> m(P_eff, 0.0);
+    std::vector<uint8_t> known(P_eff, 0), dropped;
+    auto run_tests = [&](const std::vector<uint8_t>& running) -> aqs_status {
+      std::vector<CmpJob> cj;
+      std::vector<int> idx;
+      for (int i = 1; i < P_eff; i++) {
+        if (known[i] || running[i - 1] || c->st[i - 1].status != AQS_OK || c->st[i].step < 1)
+          continue;
+        AQS_TRY(gather_user(c, i - 1, c->ends + per * (i - 1)));
+        CmpJob J;
+        J.a = c->ends + per * (i - 1);
+        J.b = c->d_snap + (size_t)c->dim * c->nmax * i;
+        J.sa = D;
+        J.sc = 1;
+        J.sb = D;
+        J.sc2 = 1;
+        std::memcpy(J.H, c->geom[i - 1].H, sizeof(J.H));  // both at strain i K dgamma
+        J.n = n;
+        cj.push_back(J);
+        idx.push_back(i);
+      }
+      if (cj.empty()) return AQS_OK;
+      std::vector<double> v(cj.size());
+      CUDA_TRY(cudaMemcpyAsync(c->d_jobs, cj.data(), sizeof(CmpJob) * cj.size(),
+                               cudaMemcpyHostToDevice, c->stream));
+      CUDA_TRY(launch_compare(D, c->d_jobs, (int)cj.size(), c->d_cmp, c->stream));
+      CUDA_TRY(cudaMemcpyAsync(v.data(), c->d_cmp, sizeof(double) * cj.size(),
+                               cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(cudaStreamSynchronize(c->stream));
+      for (size_t k = 0; k < idx.size(); k++) {
+        m[idx[k]] = v[k];
+        known[idx[k]] = 1;
+      }
+      return AQS_OK;
+    };
+    PassHook hook = [&](std::vector<int>& next, std::vector<uint8_t>& drop) -> aqs_status {
+      std::vector<uint8_t> running(c->R, 0);
+      for (int r : next) running[r] = 1;
+      AQS_TRY(run_tests(running));
+      int fail_at = P_eff;
+      for (int i = 1; i < P_eff; i++)
+        if (known[i] && !(m[i] < eq_tol)) {
+          fail_at = i;
+          break;
+        }
+      if (fail_at < P_eff) {
+        std::vector<int> keep;
+        for (int r : next) {
+          if (r >= fail_at) drop[r] = 1;
+          else keep.push_back(r);
+        }
+        next.swap(keep);
+      }
+      return AQS_OK;
+    };
     JobOut jo;
-    AQS_TRY(run_jobs(c, f, jobs, &jo));
+    AQS_TRY(run_jobs(c, f, jobs, &jo, nullptr, p->run_discarded ? nullptr : &hook, &dropped));
     for (int i = 0; i < P_eff; i++) {
       const double* rec = &jo.rec[(size_t)i * jo.stride * kRecFields];
-      out->fire_iters_total += (int64_t)rec[3];
-      out->evals64_total += (int64_t)rec[4];
-      for (int k = 0; k < Ki[i]; k++) {
+      // steps this chain completed (all of them unless it was stopped)
+      const int64_t done = dropped[i] ? c->st[i].step : 1 + Ki[i];
+      if (dropped[i]) out->chains_stopped++;
+      if (done >= 1) {
+        out->fire_iters_total += (int64_t)rec[3];
+        out->evals64_total += (int64_t)rec[4];
+      }
+      for (int k = 0; k < Ki[i] && k + 1 < done; k++) {
         const double* q = rec + (size_t)(k + 1) * kRecFields;
         cE[(size_t)i * K + k] = q[0];
         cT[(size_t)i * K + k] = q[1];
@@ -1226,32 +1307,11 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
         out->evals64_total += (int64_t)q[4];
       }
     }
-    // sequential equality check (Eq. 20): end of chain i-1 vs F(r^c_iK)
-    std::vector<double> m(P_eff, 0.0);
-    if (P_eff > 1) {
-      std::vector<CmpJob> jobs(P_eff - 1);
-      for (int i = 1; i < P_eff; i++) {
-        AQS_TRY(gather_user(c, i - 1, c->ends + per * (i - 1)));
-        CmpJob& J = jobs[i - 1];
-        J.a = c->ends + per * (i - 1);
-        J.b = c->d_snap + (size_t)c->dim * c->nmax * i;
-        J.sa = D;
-        J.sc = 1;
-        J.sb = D;
-        J.sc2 = 1;
-        std::memcpy(J.H, c->geom[i - 1].H, sizeof(J.H));  // both at strain i K dgamma
-        J.n = n;
-      }
-      CUDA_TRY(cudaMemcpyAsync(c->d_jobs, jobs.data(), sizeof(CmpJob) * jobs.size(),
-                               cudaMemcpyHostToDevice, c->stream));
-      CUDA_TRY(launch_compare(D, c->d_jobs, (int)jobs.size(), c->d_cmp, c->stream));
-      CUDA_TRY(cudaMemcpyAsync(m.data() + 1, c->d_cmp, sizeof(double) * (P_eff - 1),
-                               cudaMemcpyDeviceToHost, c->stream));
-      CUDA_TRY(cudaStreamSynchronize(c->stream));
-    }
+    if (P_eff > 1) AQS_TRY(run_tests(std::vector<uint8_t>(c->R, 0)));
     int first_fail = -1;
     int64_t q = Ki[0];
     for (int i = 1; i < P_eff; i++) {
+      if (!known[i]) return fail(AQS_ERR_CUDA, "internal: equality test %d was not made", i);
       bool eq = m[i] < eq_tol;
       if (out->n_log < out->log_cap) {
         int64_t j = out->n_log;

@@ -334,3 +334,30 @@ def test_lean_launch_2d_matches_register_launch(A, syn, prec):
     np.testing.assert_allclose(a["E"], b["E"], rtol=rel)
     assert np.array_equal(a["D"] > EV_THR, b["D"] > EV_THR)
     assert mi_disp(sa.positions(), sb.positions(), sb.box()) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_stopping_discarded_chains_keeps_decisions(A, syn, glass256, prec):
+    """Chains whose results a failed equality test has already discarded stop
+    early by default; the decision log, energies and final minimum are those
+    of running every chain to its end (and of the stored oracle run)."""
+    gold = load_golden("par_2d_n256_s0.npz")
+    x, t, H = glass256["x"], glass256["types"], glass256["H"]
+    P = A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED
+    out = []
+    for run_discarded in (0, 1):
+        s = make_system(A, syn, x, t, H, P)
+        r = s.parallel_step(float(gold["dgamma"]), int(gold["K"]), int(gold["P"]),
+                            int(gold["n_steps"]), eq_tol=float(gold["eq_tol"]),
+                            run_discarded=run_discarded)
+        out.append((r, s.positions()))
+    (a, xa), (b, xb) = out
+    # whether a chain can be stopped depends on which chains finish first;
+    # the decisions may not depend on it
+    assert a["rejections"] > 0 and a["chains_stopped"] >= 0
+    assert b["chains_stopped"] == 0
+    for key in ("log_i", "log_eq", "log_iter"):
+        assert np.array_equal(a[key], b[key]) and np.array_equal(a[key], gold[key])
+    rel = 1e-9 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(a["E"], b["E"], rtol=rel)
+    assert mi_disp(xa, xb, gold["H"]) < 1e-6
