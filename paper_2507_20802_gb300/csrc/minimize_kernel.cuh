@@ -61,6 +61,9 @@ __device__ __forceinline__ float phi32(const Coef32& c, float s) {
 //   (s^-n - s0^-n) / ds = -u w sum_{k<n} u^k w^(n-1-k)
 //   (s^-1/2 - s0^-1/2) / ds = -(ab)^2 / (a + b),  a = s^-1/2, b = s0^-1/2
 //   dF = phi(s) e + [phi(s) - phi(s0)] d0
+// A pair that crosses the cutoff (in the list but inside at only one of the
+// two separations) uses the plain difference, with phi = 0 outside.  The
+// function has no branches, so the lanes of a warp never diverge on it.
 template <int D>
 __device__ __forceinline__ void pair_dev(const Coef32& c, const float* d0, const float* e,
                                          float* F) {
@@ -70,31 +73,24 @@ __device__ __forceinline__ void pair_dev(const Coef32& c, const float* d0, const
     s0 = fmaf(d0[k], d0[k], s0);
     ds = fmaf(e[k], fmaf(2.0f, d0[k], e[k]), ds);
   }
-  float s = s0 + ds;
-  bool in0 = s0 < c.rc2f, in1 = s < c.rc2f;
-  if (in0 && in1) {
-    float a = rsqrtf(s), b = rsqrtf(s0);
-    float u = a * a, w = b * b;
-    float w2 = w * w, w3 = w2 * w, w4 = w2 * w2, w5 = w4 * w, w6 = w3 * w3;
-    float h4 = fmaf(u, fmaf(u, w + u, w2), w3);
-    float h7 = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, w + u, w2), w3), w4), w5), w6);
-    float uw = u * w;
-    float ab = a * b;
-    float dh = -(ab * ab) / (a + b);
-    float u2 = u * u, u4 = u2 * u2, u7 = u4 * u2 * u;
-    float phi = fmaf(c.Af, u7, fmaf(c.Bf, u4, c.Cf * a));
-    float dphi = ds * fmaf(-c.Af * uw, h7, fmaf(-c.Bf * uw, h4, c.Cf * dh));
+  const float s = s0 + ds;
+  const bool in0 = s0 < c.rc2f, in1 = s < c.rc2f;
+  const float a = rsqrtf(s), b = rsqrtf(s0);
+  const float u = a * a, w = b * b;
+  const float w2 = w * w, w3 = w2 * w, w4 = w2 * w2, w5 = w4 * w, w6 = w3 * w3;
+  const float h4 = fmaf(u, fmaf(u, w + u, w2), w3);
+  const float h7 = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, w + u, w2), w3), w4), w5), w6);
+  const float uw = u * w;
+  const float ab = a * b;
+  const float dh = -__fdividef(ab * ab, a + b);
+  const float u2 = u * u, u4 = u2 * u2, u7 = u4 * u2 * u;
+  float phi = fmaf(c.Af, u7, fmaf(c.Bf, u4, c.Cf * a));
+  const float phi0 = fmaf(c.Af, w4 * w3, fmaf(c.Bf, w4, c.Cf * b));
+  const float dd = ds * fmaf(-c.Af * uw, h7, fmaf(-c.Bf * uw, h4, c.Cf * dh));
+  phi = in1 ? phi : 0.0f;
+  const float dphi = (in0 && in1) ? dd : phi - (in0 ? phi0 : 0.0f);
 #pragma unroll
-    for (int k = 0; k < D; k++) F[k] += fmaf(phi, e[k], dphi * d0[k]);
-  } else if (in1) {
-    float phi = phi32(c, s);
-#pragma unroll
-    for (int k = 0; k < D; k++) F[k] = fmaf(phi, d0[k] + e[k], F[k]);
-  } else if (in0) {
-    float phi = phi32(c, s0);
-#pragma unroll
-    for (int k = 0; k < D; k++) F[k] = fmaf(-phi, d0[k], F[k]);
-  }
+  for (int k = 0; k < D; k++) F[k] += fmaf(phi, e[k], dphi * d0[k]);
 }
 
 // Published record of one atom in shared memory.  EVAL64 reads q64 (FP64
@@ -389,9 +385,8 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
   auto nbrec = [&](uint32_t ent) -> const Pub<D>* {
     const int ow = nb_owner(ent), sl = nb_slot(ent);
     if (MEM == 2) return pub + ow * npc + sl;
-    if (ow == rank) return mine + sl;
     if (GREC) return pubg + (g.off + (int64_t)ow * npc + sl);
-    return rpub[ow] + sl;
+    return ow == rank ? mine + sl : rpub[ow] + sl;
   };
   // MEM 2: copy the records of the other CTAs that own neighbours (16-byte words)
   auto stage = [&]() {
@@ -740,23 +735,28 @@ __global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
       } else {
         float qi[3], di[3], f[3] = {0.f, 0.f, 0.f};
         load_pub32<D>(&mine[li], qi, di);
-        // the two species rows of this atom in registers (A.nt <= 2)
-        const Coef32 c0 = coef32(coef[ti * A.nt]);
-        const Coef32 c1 = A.nt > 1 ? coef32(coef[ti * A.nt + 1]) : c0;
+        auto pair_loop = [&](auto coef_of) {
 #pragma unroll 4
-        for (int j = 0; j < nn; j++) {
-          uint32_t ent = LSM ? lst[j * lstride + li] : __ldcs(row + (int64_t)j * n);
-          float qj[3], dj[3], d0[3], e[3];
-          load_pub32<D>(nbrec(ent), qj, dj);
-          const float* of = off32l + 3 * 32 * nb_code(ent) + lane;
+          for (int j = 0; j < nn; j++) {
+            uint32_t ent = LSM ? lst[j * lstride + li] : __ldcs(row + (int64_t)j * n);
+            float qj[3], dj[3], d0[3], e[3];
+            load_pub32<D>(nbrec(ent), qj, dj);
+            const float* of = off32l + 3 * 32 * nb_code(ent) + lane;
 #pragma unroll
-          for (int c = 0; c < D; c++) {
-            d0[c] = (qj[c] - qi[c]) + of[c * 32];
-            e[c] = dj[c] - di[c];
+            for (int c = 0; c < D; c++) {
+              d0[c] = (qj[c] - qi[c]) + of[c * 32];
+              e[c] = dj[c] - di[c];
+            }
+            pair_dev<D>(coef_of(nb_type(ent)), d0, e, f);
           }
-          const int tj = nb_type(ent);
-          const Coef32 cj = A.nt <= 2 ? (tj ? c1 : c0) : coef32(coef[ti * A.nt + tj]);
-          pair_dev<D>(cj, d0, e, f);
+        };
+        if (A.nt <= 2) {
+          // the two species rows of this atom in registers
+          const Coef32 c0 = coef32(coef[ti * A.nt]);
+          const Coef32 c1 = A.nt > 1 ? coef32(coef[ti * A.nt + 1]) : c0;
+          pair_loop([&](int tj) { return tj ? c1 : c0; });
+        } else {
+          pair_loop([&](int tj) { return coef32(coef[ti * A.nt + tj]); });
         }
         float f2 = 0.f, pv = 0.f, v2 = 0.f, dd = 0.f;
 #pragma unroll
