@@ -323,6 +323,8 @@ def main():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--baseline-steps", type=int, default=2)
     ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d"], default="cfg1")
+    ap.add_argument("--launch-budget", type=int, default=2048,
+                    help="FIRE iterations per persistent launch")
     ap.add_argument("--autotune", type=int, default=300,
                     help="FIRE iterations per autotuner candidate (0: size rule only)")
     ap.add_argument("--quench-iters", type=int, default=400000)
@@ -360,6 +362,7 @@ def main():
         # the chains tune cluster size and staging during the first (untimed)
         # warm-up pass
         s.set_autotune(args.autotune)
+    s.set_launch_budget(args.launch_budget)
     fire = A.fire_params()
     n_total = int(round(GAMMA_END / DGAMMA))
     done = 0
@@ -505,6 +508,7 @@ def main():
                 "fp64_sequential_gpu_baseline": base,
                 "detail": {"accepted_steps": int(total_steps), "rejections": rej,
                            "chains_stopped_early": stopped, "autotune_iters": args.autotune,
+                           "launch_budget": args.launch_budget,
                            "wall_s": wall, "fire_iters_per_step": mean_iters,
                            "fp32_evals": st["evals32"], "fp64_evals": st["evals64"],
                            "rebuilds_in_kernel": st["rebuilds"],

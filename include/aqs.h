@@ -351,6 +351,14 @@ aqs_status aqs_autotune_clusters(aqs_system* sys, const aqs_fire_params* fire, i
  * size rule: C = min(16, 152 / replicas), at least ceil(N / 4096)).  Ignored
  * when the system was created with an explicit cluster_size. */
 aqs_status aqs_set_autotune(aqs_system* sys, int64_t iters);
+/* FIRE iterations (>= 1, default 2048) each replica runs per persistent
+ * launch before control returns to the host, which then gives the replicas
+ * still running larger clusters and stops discarded level-II chains.
+ * Shorter launches use the GPU better when replicas finish at different
+ * times, at the cost of a host round trip and one FP64 force evaluation per
+ * replica per launch.  Results agree within the precision's tolerance (the
+ * FP64 re-reference points move).  Applies to the system and its chains. */
+aqs_status aqs_set_launch_budget(aqs_system* sys, int64_t iters);
 /* Fixes the staging mode (0..3) of this system and its chains, or -1 for the
  * automatic choice.  AQS_ERR_INVALID_ARG outside -1..3. */
 aqs_status aqs_set_staging(aqs_system* sys, int mode);

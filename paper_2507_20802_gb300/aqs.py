@@ -131,6 +131,7 @@ _SIGS = {
                                         C.POINTER(C.c_int), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]),
     "aqs_set_autotune": (C.c_int, [C.c_void_p, C.c_int64]),
+    "aqs_set_launch_budget": (C.c_int, [C.c_void_p, C.c_int64]),
     "aqs_set_staging": (C.c_int, [C.c_void_p, C.c_int]),
     "aqs_staging": (C.c_int, [C.c_void_p, C.c_int]),
     "aqs_set_kernel_timing": (None, [C.c_int]),
@@ -510,6 +511,9 @@ class System:
                                           m, C.byref(best), C.byref(mode), _dp(ms), _dp(mm)))
         return (best.value, mode.value, {c: float(ms[c]) for c in range(1, 17) if ms[c] >= 0},
                 {k: float(mm[k]) for k in range(4) if mm[k] >= 0})
+
+    def set_launch_budget(self, iters):
+        check(lib().aqs_set_launch_budget(self.h, C.c_int64(iters)))
 
     def set_staging(self, mode):
         check(lib().aqs_set_staging(self.h, int(mode)))

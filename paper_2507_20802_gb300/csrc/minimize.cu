@@ -41,9 +41,9 @@ size_t minimize_smem_bytes(int dim, int npc, int nrep, int nt, int cap, int mem)
   return minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, mem);
 }
 
-int minimize_atoms_per_thread(int npc) {
+int minimize_atoms_per_thread(int dim, int npc) {
   int apt = 0, threads = 0;
-  choose_apt(npc, &apt, &threads);
+  choose_apt(dim, npc, &apt, &threads);
   return apt;
 }
 

@@ -67,8 +67,9 @@ size_t minimize_smem_bytes(int dim, int npc, int nrep, int nt, int cap, int mem)
 int minimize_staging(int dim, int npc, int nrep, int nt, int cap, int want);
 cudaError_t launch_minimize(int dim, bool mixed, MinArgs a, int n_clusters, int C, int npc,
                             int nrep, int cap, cudaStream_t s, int staging = -1);
-// atoms per thread of a launch with npc atoms per CTA (1, 2, 4 or 8)
-int minimize_atoms_per_thread(int npc);
+// atoms per thread of a launch with npc atoms per CTA (1, 2, 4 or 8; lean
+// launches use up to 1024 threads, the others up to 512)
+int minimize_atoms_per_thread(int dim, int npc);
 // launches that keep the per-atom state in MinArgs::lean32 / lean64 instead
 // of registers (where registers would spill)
 constexpr bool minimize_is_lean(int dim, int apt) { return apt >= 4 || (dim == 3 && apt >= 2); }

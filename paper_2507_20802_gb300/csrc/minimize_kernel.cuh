@@ -201,7 +201,7 @@ constexpr double kBigV2 = 1e30;
 // that own neighbours copied into the local shared memory, so the force loop
 // reads local shared memory only.
 template <int D, bool MIXED, int APT, int MEM>
-__global__ void __launch_bounds__(512, 1) k_minimize(MinArgs A) {
+__global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_minimize(MinArgs A) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();

@@ -27,8 +27,11 @@ inline int choose_mem(int dim, int npc, int nrep, int nt, int cap, int want = -1
   return 0;
 }
 
-inline void choose_apt(int npc, int* apt, int* threads) {
+inline void choose_apt(int dim, int npc, int* apt, int* threads) {
   *apt = npc <= 512 ? 1 : (npc <= 1024 ? 2 : (npc <= 2048 ? 4 : 8));
+  // lean launches hold little per-thread state and may use up to 1024
+  // threads: halve the atoms per thread where the result is still lean
+  if (minimize_is_lean(dim, *apt) && minimize_is_lean(dim, *apt / 2)) *apt /= 2;
   int t = (npc + *apt - 1) / *apt;
   *threads = ((t + 31) / 32) * 32;
 }
@@ -64,8 +67,8 @@ template <int D, bool MIXED, int MEM>
 cudaError_t run_apt(const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
                            cudaStream_t s, int* max_clusters) {
   int apt, threads;
-  choose_apt(npc, &apt, &threads);
-  if (threads > 512) return cudaErrorInvalidValue;
+  choose_apt(D, npc, &apt, &threads);
+  if (threads > (minimize_is_lean(D, apt) ? 1024 : 512)) return cudaErrorInvalidValue;
   switch (apt) {
     case 1: return run_t<D, MIXED, 1, MEM>(a, n_clusters, C, threads, smem, s, max_clusters);
     case 2: return run_t<D, MIXED, 2, MEM>(a, n_clusters, C, threads, smem, s, max_clusters);

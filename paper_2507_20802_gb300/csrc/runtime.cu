@@ -72,6 +72,9 @@ struct aqs_system {
   // a mode the caller fixed, which the tuner leaves alone
   int staging = -1;
   bool staging_user = false;
+  // FIRE iterations a replica runs per persistent launch before the host
+  // regroups the replicas still running (larger clusters, stopped chains)
+  int64_t launch_budget = 2048;
   aqs_potential pot{};
   double skin = 0.3, rcmax = 0.0, rlist = 0.0;
   cudaStream_t stream = nullptr;
@@ -439,7 +442,7 @@ MinArgs min_args(aqs_system* s, const aqs_fire_params* f) {
   a.fire = fire_dev(f);
   a.skin = s->skin;
   a.rlist = s->rlist;
-  a.launch_budget = 2048;
+  a.launch_budget = s->launch_budget;
   a.npc_launch = 0;
   a.nrep_launch = 0;
   a.rec = s->d_rec;
@@ -595,7 +598,7 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
     if (!s->lean32) {
       bool lean = false;
       for (int r : todo)
-        lean = lean || minimize_is_lean(s->dim, minimize_atoms_per_thread(s->geom[r].npc));
+        lean = lean || minimize_is_lean(s->dim, minimize_atoms_per_thread(s->dim, s->geom[r].npc));
       if (lean) {
         AQS_TRY(alloc_arr(s, &s->lean32, (size_t)15 * s->ntot));
         AQS_TRY(alloc_arr(s, &s->lean64, (size_t)3 * s->ntot));
@@ -945,6 +948,7 @@ aqs_status ensure_chains(aqs_system* s, int src, int P) {
     return fail(AQS_ERR_OOM, "chain snapshot allocation failed");
   }
   c->tune_iters = s->tune_iters;
+  c->launch_budget = s->launch_budget;
   c->staging = s->staging_user ? s->staging : -1;
   c->staging_user = s->staging_user;
   s->chains = c;
@@ -1498,6 +1502,13 @@ aqs_status aqs_autotune_clusters(aqs_system* s, const aqs_fire_params* f, int64_
   if (best > 0) s->tuned[std::make_pair(cnt, nmax)] = std::make_pair(best, mode);
   if (best_cluster) *best_cluster = best;
   if (best_staging) *best_staging = mode;
+  return AQS_OK;
+}
+
+aqs_status aqs_set_launch_budget(aqs_system* s, int64_t iters) {
+  if (!s || iters < 1) return fail(AQS_ERR_INVALID_ARG, "set_launch_budget: iters must be >= 1");
+  s->launch_budget = iters;
+  if (s->chains) s->chains->launch_budget = iters;
   return AQS_OK;
 }
 
