@@ -53,6 +53,17 @@ RC_FACTOR = 2.5
 DENSITY = 1.2
 FRACTION_A = {2: 0.65, 3: 0.80}
 
+# The paper's own binary glass (Sec. 2.2): small (S, type 0) and large (L,
+# type 1) discs with sigma_SS = 2 sin(pi/10), sigma_LL = 2 sin(pi/5),
+# sigma_SL = 1, eps_SS = eps_SL = 1/2, eps_LL = 1, number density 1 and
+# N_L / N_S = (1 + sqrt 5) / 4 (so N = 400 has N_S = 221, N_L = 179 by
+# rounding).  The same shifted-force cutoff 2.5 sigma_ab is used.
+SL_SIGMA = np.array([[2.0 * math.sin(math.pi / 10.0), 1.0],
+                     [1.0, 2.0 * math.sin(math.pi / 5.0)]])
+SL_EPS = np.array([[0.5, 0.5], [0.5, 1.0]])
+SL_DENSITY = 1.0
+SL_FRACTION_S = 1.0 / (1.0 + (1.0 + math.sqrt(5.0)) / 4.0)
+
 # FIRE settings of the workloads (dt0, alpha0, f_inc, f_dec given by the
 # workload; the remaining ones are the standard FIRE choices)
 FIRE = dict(dt0=0.005, alpha0=0.1, f_inc=1.1, f_dec=0.5, f_alpha=0.99, dt_max=0.05,

@@ -14,6 +14,9 @@ Each file is an .npz of FP64/int arrays:
   observables, decision log, final positions.
 * aqs_3d_n2048_s0.npz -- three sequential AQS steps of the 3D glass,
   dgamma = 5e-5.
+* glass_sl_n400_s0.npz, aqs_sl_n400_s0.npz -- the paper's S/L glass (N = 400,
+  density 1, Sec. 2.2) quenched by the oracle, and 20 sequential AQS steps
+  of the paper's increment dgamma = 1/200 (Sec. 4).
 
 Usage: python tests/golden/make_golden.py [name ...]   (default: all)
 """
@@ -83,6 +86,30 @@ def job_aqs3d2048():
     r = oracle.aqs(_pot(3), _fire(), g["x"], g["types"], g["H"], 5e-5, 3)
     assert r["status"] == 0
     np.savez(os.path.join(HERE, "aqs_3d_n2048_s0.npz"), dgamma=5e-5, n_steps=3, **r)
+
+
+def _pot_sl():
+    return oracle.make_potential(2, syn.SL_SIGMA, syn.SL_EPS, syn.RC_FACTOR)
+
+
+def glass_sl(n, seed):
+    path = os.path.join(HERE, f"glass_sl_n{n}_s{seed}.npz")
+    if os.path.exists(path):
+        return dict(np.load(path))
+    x, t, H = syn.random_glass_start(n, 2, seed, fraction_a=syn.SL_FRACTION_S,
+                                     density=syn.SL_DENSITY)
+    r = oracle.fire(_pot_sl(), _fire(), x, t, H)
+    assert r["status"] == 0, r["status"]
+    out = dict(x=r["x"], types=t, H=H, E=r["E"], iters=r["iters"], fmax=r["fmax"])
+    np.savez(path, **out)
+    return out
+
+
+def job_aqssl400():
+    g = glass_sl(400, 0)
+    r = oracle.aqs(_pot_sl(), _fire(), g["x"], g["types"], g["H"], 1.0 / 200.0, 20)
+    assert r["status"] == 0
+    np.savez(os.path.join(HERE, "aqs_sl_n400_s0.npz"), dgamma=1.0 / 200.0, n_steps=20, **r)
 
 
 JOBS = {k[4:]: v for k, v in globals().items() if k.startswith("job_")}

@@ -361,3 +361,21 @@ def test_stopping_discarded_chains_keeps_decisions(A, syn, glass256, prec):
     rel = 1e-9 if prec == "fp64" else 1e-6
     np.testing.assert_allclose(a["E"], b["E"], rtol=rel)
     assert mi_disp(xa, xb, gold["H"]) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_paper_sl_glass_trajectory_matches_golden(A, syn, prec):
+    """The paper's S/L glass (N = 400, density 1, Sec. 2.2) through 20 AQS
+    steps of its increment dgamma = 1/200 (every step plastic at this
+    increment) against the stored oracle run."""
+    g = load_golden("glass_sl_n400_s0.npz")
+    gold = load_golden("aqs_sl_n400_s0.npz")
+    P = A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED
+    s = A.System(np.asarray(g["x"], float), g["types"], g["H"][None], [len(g["x"])],
+                 syn.SL_SIGMA, syn.SL_EPS, syn.RC_FACTOR, precision=P)
+    out = s.run_sequential(float(gold["dgamma"]), int(gold["n_steps"]))
+    rel = 1e-9 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(out["E"][:, 0], gold["E"], rtol=rel)
+    np.testing.assert_allclose(out["D"][:, 0], gold["D"], rtol=1e-4)
+    assert mi_disp(s.positions(), gold["x"], gold["H"]) < 1e-6
+    np.testing.assert_allclose(s.box(), gold["H"], rtol=1e-12)
