@@ -51,8 +51,8 @@ FLOP32_PER_PAIR = 62
 FLOP64_PER_PAIR = 32
 # mean FIRE iterations per accepted fine step of this workload, used only to
 # express the reference arm's oracle sample in steps/s (measured by this
-# benchmark's own arm; see profiles/bench_cfg1_n4096.md)
-ITERS_PER_STEP_REF = 21000
+# benchmark's own arm on the seed-0 glass)
+ITERS_PER_STEP_REF = 23000
 
 CONFIG = {"workload": "2D binary LJ glass (65:35, rho=1.2), N=4096, Algorithm 1 with P=16 "
                       "chains of K=10 fine steps, dgamma=1e-4, FIRE to |F|max<1e-10, mixed "
@@ -195,6 +195,63 @@ def _line(metric, value, unit, args, ms, config, extra):
     print(json.dumps(d), flush=True)
 
 
+def run_seeds(args):
+    """Metric 1 over several glasses: for seeds 0..n-1 the FP64-quenched glass,
+    one warm-up pass (autotuning the chains) and `steps` timed passes of
+    Algorithm 1; prints one line with the per-seed values, their mean and
+    standard deviation (device time, same workload as the default line)."""
+    import torch
+    from paper_2507_20802_gb300 import aqs as A, synthetic as syn
+    torch.cuda.set_device(0)
+    vals, accepted_all, ms_all = [], [], 0.0
+    for seed in range(args.seeds):
+        x, t, H = syn.random_glass_start(N_ATOMS, 2, seed=seed)
+        g = A.System(x, t, H[None], [N_ATOMS], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
+                     precision=A.AQS_FP64)
+        q = g.minimize(A.fire_params(max_iter=2_000_000))[0]
+        assert q["status"] == 0, q
+        xq, Hq = g.positions(), g.box()
+        g.close()
+        s = A.System(xq, t, Hq[None], [N_ATOMS], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
+                     precision=A.AQS_MIXED)
+        if args.autotune > 0:
+            s.set_autotune(args.autotune)
+        s.set_launch_budget(args.launch_budget)
+        n_total = int(round(GAMMA_END / DGAMMA))
+        done = 0
+
+        def one_pass():
+            nonlocal done
+            r = s.parallel_step(DGAMMA, K_FINE, P_CHAINS, max(1, n_total - done),
+                                max_iterations=1)
+            done += r["accepted"]
+            return r
+        for _ in range(max(1, args.warmup)):
+            one_pass()
+        acc, ms = 0, 0.0
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = one_pass()
+            e1.record()
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            acc += r["accepted"]
+        vals.append(acc / (ms / 1e3))
+        accepted_all.append(acc)
+        ms_all += ms
+        s.close()
+    v = np.array(vals)
+    config = dict(CONFIG, seeds=list(range(args.seeds)),
+                  l2="not flushed (seed statistics; the default line flushes)")
+    _line(METRIC + ", mean over glasses", float(v.mean()), UNIT, args,
+          ms_all / max(1, args.seeds * args.steps), config,
+          {"per_seed": [float(a) for a in v], "std": float(v.std(ddof=1)) if len(v) > 1 else 0.0,
+           "accepted_per_seed": accepted_all,
+           "note": "one warm-up pass then the timed passes, each glass from the same strain"})
+
+
 def run_batch64(args):
     """64 independent 2D glasses of log-uniform size in [1024, 16384] (sizes
     from stream seed 2, glass r from seed 1000 + r), plain AQS dgamma = 5e-5,
@@ -323,6 +380,8 @@ def main():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--baseline-steps", type=int, default=2)
     ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d"], default="cfg1")
+    ap.add_argument("--seeds", type=int, default=0,
+                    help="> 0: Metric 1 over glasses of seeds 0..n-1 (mean and std)")
     ap.add_argument("--launch-budget", type=int, default=2048,
                     help="FIRE iterations per persistent launch")
     ap.add_argument("--autotune", type=int, default=300,
@@ -333,6 +392,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.seeds > 0:
+        return run_seeds(args) or 0
     if args.workload == "batch64":
         return run_batch64(args) or 0
     if args.workload == "glass3d":
