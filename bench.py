@@ -53,6 +53,15 @@ FLOP64_PER_PAIR = 32
 # express the reference arm's oracle sample in steps/s (measured by this
 # benchmark's own arm on the seed-0 glass)
 ITERS_PER_STEP_REF = 23000
+# DRAM bytes (read + write) of the dominant kernel from one ncu capture each
+# (--set full, clocks unlocked), for the roofline's "traffic"; a capture is
+# valid only for the kernel version it was taken on.
+#   Algorithm 1 (2D, N = 4096): one level-II chain launch of 45.6 ms, on chip
+TRAFFIC_CFG1_PER_LAUNCH = 11_975_680
+#   3D (N = 65536): the timed launch of 6 replicas x 200 iterations (35.04 GB
+#   read + 0.37 GB written), per replica-iteration; the bench scales it by the
+#   replica-iterations of its launch
+TRAFFIC_3D_PER_REPLICA_ITER = 29_508_000
 
 CONFIG = {"workload": "2D binary LJ glass (65:35, rho=1.2), N=4096, Algorithm 1 with P=16 "
                       "chains of K=10 fine steps, dgamma=1e-4, FIRE to |F|max<1e-10, mixed "
@@ -371,7 +380,9 @@ def run_glass3d(args):
           1e3 * secs, config,
           {"gpu_launches": A.aqs_launch_count() - l0, "clocks": clk.summary(),
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                        "frac": gbs / peak, "traffic": None,
+                        "frac": gbs / peak,
+                        "traffic": (TRAFFIC_3D_PER_REPLICA_ITER * iters / max(1, st["launches"])
+                                    if TRAFFIC_3D_PER_REPLICA_ITER else None),
                         "note": "algorithmic bytes = 4 per list entry visited + 28 per atom per FP32 evaluation"},
            "detail": {"mean_neighbours": nb, "quench_iters": q["iters"],
                       "quench_fmax": q["fmax"], "fp32_evals": st["evals32"],
@@ -518,7 +529,9 @@ def main():
     achieved = flop32 / kern_s / 1e12 if kern_s > 0 else 0.0
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": None, "kernel": "k_minimize<2,mixed>",
+                "traffic": TRAFFIC_CFG1_PER_LAUNCH,
+                "traffic_note": "bytes per launch, ncu capture of one level-II chain launch",
+                "kernel": "k_minimize<2,mixed>",
                 "kernel_share_of_step": kern_s / secs if secs > 0 else None,
                 "fp64_tflops": flop64 / kern_s / 1e12 if kern_s > 0 else 0.0,
                 "launches": st["launches"], "avg_launch_ms": st["kernel_ms"] / max(1, st["launches"]),
