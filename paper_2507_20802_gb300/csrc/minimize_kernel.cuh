@@ -304,6 +304,9 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
   // atom being processed is in registers: FP32 reference position, displacement, velocity, reference
   // force and the force used by the update, and the FP64 force.
   constexpr bool LEAN = minimize_is_lean(D, APT);
+  // pair-loop unrolling: lean launches keep more list and record loads in
+  // flight per thread (they stream the lists from HBM)
+  constexpr int kPairUnroll = LEAN ? 8 : 4;
   constexpr int AR = LEAN ? 1 : APT;
   int ty[APT];
   float q32[AR][3], d32[AR][3], v32[AR][3], fr32[AR][3], Fu[AR][3];
@@ -736,7 +739,7 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
         float qi[3], di[3], f[3] = {0.f, 0.f, 0.f};
         load_pub32<D>(&mine[li], qi, di);
         auto pair_loop = [&](auto coef_of) {
-#pragma unroll 4
+#pragma unroll kPairUnroll
           for (int j = 0; j < nn; j++) {
             uint32_t ent = LSM ? lst[j * lstride + li] : __ldcs(row + (int64_t)j * n);
             float qj[3], dj[3], d0[3], e[3];
