@@ -58,10 +58,10 @@ ITERS_PER_STEP_REF = 23000
 # valid only for the kernel version it was taken on.
 #   Algorithm 1 (2D, N = 4096): one level-II chain launch of 45.6 ms, on chip
 TRAFFIC_CFG1_PER_LAUNCH = 11_975_680
-#   3D (N = 65536): the timed launch of 6 replicas x 200 iterations (35.04 GB
-#   read + 0.37 GB written), per replica-iteration; the bench scales it by the
+#   3D (N = 65536): the timed launch of 6 replicas x 200 iterations (36.10 GB
+#   read + 0.42 GB written), per replica-iteration; the bench scales it by the
 #   replica-iterations of its launch
-TRAFFIC_3D_PER_REPLICA_ITER = 29_508_000
+TRAFFIC_3D_PER_REPLICA_ITER = 30_438_000
 
 CONFIG = {"workload": "2D binary LJ glass (65:35, rho=1.2), N=4096, Algorithm 1 with P=16 "
                       "chains of K=10 fine steps, dgamma=1e-4, FIRE to |F|max<1e-10, mixed "
