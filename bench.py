@@ -261,6 +261,82 @@ def run_seeds(args):
            "note": "one warm-up pass then the timed passes, each glass from the same strain"})
 
 
+def run_warm(args):
+    """The learned warm start's kernels at the inference size of the warm-start
+    workload (32 replicas x 16384 atoms = 524288 per-atom rows): BF16
+    tensor-core MLP forward (66 -> 128 -> 128 -> 128 -> 2), fused forward +
+    backward + AdamW training step on 65536-row batches, and the FP64
+    neighbour-shell features of the same 524288 atoms.  value = inference rows/s."""
+    import torch
+    from paper_2507_20802_gb300 import aqs as A, synthetic as syn
+    torch.cuda.set_device(0)
+    R, n = 32, 16384
+    rows = R * n
+    flop_fwd = 2 * (66 * 128 + 2 * 128 * 128 + 128 * 2)  # algorithmic, per row
+    g = torch.Generator(device="cpu").manual_seed(0)
+    feat = (torch.randn((rows, A.WARM_IN), generator=g) * 0.5).to(torch.bfloat16).cuda()
+    feat[:, 66:] = 0
+    target = torch.randn((rows, 2), generator=g).cuda()
+    out = torch.zeros((rows, 2), dtype=torch.float32, device="cuda")
+    w = A.Warm(seed=1)
+    l0 = A.aqs_launch_count()
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    for _ in range(max(3, args.warmup)):
+        w.predict(feat, out)
+    with Clocks(0) as clk:
+        t_fwd = timed(lambda: w.predict(feat, out), max(1, args.steps) * 4)
+        batch = 65536
+        k = [0]
+
+        def step():
+            i = k[0] % (rows // batch)
+            k[0] += 1
+            w.train_step(feat[i * batch:(i + 1) * batch], target[i * batch:(i + 1) * batch], 1e-3)
+        step()
+        t_train = timed(step, max(1, args.steps) * 4)
+        # features of 32 replicas of a 16384-atom 2D configuration
+        xs, ts, Hs = [], [], []
+        for r in range(R):
+            x, t, H = syn.random_glass_start(n, 2, seed=2000 + r)
+            xs.append(x); ts.append(t); Hs.append(H)
+        sy = A.System(np.concatenate(xs), np.concatenate(ts), np.stack(Hs), [n] * R,
+                      syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR, precision=A.AQS_MIXED)
+        fb = torch.zeros((rows, A.WARM_IN), dtype=torch.bfloat16, device="cuda")
+        sy.warm_features(fb)
+        t_feat = timed(lambda: sy.warm_features(fb), max(1, args.steps))
+    peak = _peaks().get("bf16_tflops", 1900.0)
+    fwd_tf = rows * flop_fwd / t_fwd / 1e12
+    train_tf = 3 * batch * flop_fwd / t_train / 1e12
+    config = {"workload": "learned warm start: MLP 66->128->128->128->2 (BF16, FP32 accumulate) "
+                          "on 524288 per-atom rows (32 x 16384 atoms), training on 65536-row "
+                          "batches, FP64 32-neighbour features", "rows": rows,
+              "train_batch": batch, "l2": "inputs (84 MB of BF16 features) resident; not flushed"}
+    _line("warm-start inference rows/s", rows / t_fwd, "rows/s", args, 1e3 * t_fwd, config,
+          {"gpu_launches": A.aqs_launch_count() - l0, "clocks": clk.summary(),
+           "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s",
+                        "frac": fwd_tf / peak, "traffic": None,
+                        "note": "algorithmic 82944 flop per row; mma.sync BF16 (not tcgen05); "
+                                "peak = measured cuBLAS bf16 burst"},
+           "detail": {"train_step_ms": 1e3 * t_train, "train_rows_per_s": batch / t_train,
+                      "train_tflops": train_tf, "train_frac": train_tf / peak,
+                      "features_ms": 1e3 * t_feat, "features_rows_per_s": rows / t_feat}})
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
+
+
 def run_batch64(args):
     """64 independent 2D glasses of log-uniform size in [1024, 16384] (sizes
     from stream seed 2, glass r from seed 1000 + r), plain AQS dgamma = 5e-5,
@@ -401,7 +477,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--baseline-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d"], default="cfg1")
+    ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d", "warm"], default="cfg1")
     ap.add_argument("--seeds", type=int, default=0,
                     help="> 0: Metric 1 over glasses of seeds 0..n-1 (mean and std)")
     ap.add_argument("--launch-budget", type=int, default=2048,
@@ -418,6 +494,8 @@ def main():
         return run_seeds(args) or 0
     if args.workload == "batch64":
         return run_batch64(args) or 0
+    if args.workload == "warm":
+        return run_warm(args) or 0
     if args.workload == "glass3d":
         return run_glass3d(args) or 0
 
