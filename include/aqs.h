@@ -255,7 +255,8 @@ aqs_status aqs_warm_get_params(const aqs_warm* w, float* host_params);
 aqs_status aqs_warm_set_params(aqs_warm* w, const float* host_params); /* resets AdamW state */
 /* feat_bf16: device [rows][80]; feat_f64: device [rows][66] or NULL */
 aqs_status aqs_warm_features(aqs_system* sys, int replica, void* feat_bf16, double* feat_f64);
-/* out: device [rows][2] FP32 */
+/* feat_bf16: device [rows][80], 16-byte aligned (AQS_ERR_INVALID_ARG otherwise);
+ * out: device [rows][2] FP32 */
 aqs_status aqs_warm_predict(aqs_warm* w, const void* feat_bf16, int64_t rows, float* out);
 /* loss and its gradient (host, aqs_warm_num_params floats, nullable) for
  * targets (device [rows][2] FP32) */

@@ -1938,6 +1938,8 @@ aqs_status aqs_warm_features(aqs_system* s, int replica, void* feat_bf16, double
 
 aqs_status aqs_warm_predict(aqs_warm* w, const void* feat_bf16, int64_t rows, float* out) {
   if (!w || !feat_bf16 || !out || rows < 0) return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  if ((reinterpret_cast<uintptr_t>(feat_bf16) & 15u) != 0u)
+    return fail(AQS_ERR_INVALID_ARG, "features must start on a 16-byte boundary");
   if (rows == 0) return AQS_OK;
   CUDA_TRY(launch_mlp_forward(w->m, static_cast<const __nv_bfloat16*>(feat_bf16), rows, out, w->dim,
                               w->stream));

@@ -264,24 +264,133 @@ __device__ void mlp_forward_tile(const __nv_bfloat16* sw, const float* sb, const
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) k_mlp_forward(MlpDev m, const __nv_bfloat16* X, int64_t rows,
-                                                     float* Y, int nout) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(smraw);
-  __nv_bfloat16* sx = sw + MlpSmem::w1 + MlpSmem::w2 + MlpSmem::w3 + MlpSmem::w4;
-  __nv_bfloat16* sa = sx + kRows * kIn;
-  float* sb = reinterpret_cast<float*>(sa + 3 * kRows * kHid);
-  float* sz = sb + 3 * kHid + kOutPad;
-  float* zo = sz + 3 * kRows * kHid;
-  load_weights(m, sw, sb);
-  __syncthreads();
-  for (int64_t row0 = (int64_t)blockIdx.x * kRows; row0 < rows; row0 += (int64_t)gridDim.x * kRows) {
-    mlp_forward_tile(sw, sb, X, rows, row0, sx, sa, sz, zo);
-    for (int k = threadIdx.x; k < kRows * nout; k += blockDim.x) {
-      int64_t r = row0 + k / nout;
-      if (r < rows) Y[r * nout + k % nout] = zo[(k / nout) * kOutPad + k % nout];
+// ---------------------------------------------------------------------------
+// Inference (forward only).  Every warp carries 16-row tiles through the four
+// layers on its own; the weights are staged once per CTA in shared memory
+// with padded rows (88 or 136 BF16 = 176 or 272 bytes, so eight consecutive
+// rows start in different banks and ldmatrix reads them without conflicts).
+// A layer's 16 x NOUT result stays in the MMA accumulators until bias and
+// GELU are applied and it is written, as BF16, over the warp's activation
+// tile.  Arithmetic and accumulation order are those of mlp_forward_tile.
+constexpr int kInferWarps = 16;
+constexpr int kLdIn = kIn + 8;
+constexpr int kLdHid = kHid + 8;
+
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t* r, const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(a));
+}
+
+// acc[nt] = A (16 x K, BF16, row stride lda) times W^T (W: NOUT x K, row
+// stride ldw), FP32 accumulators in the mma.m16n8k16 layout
+template <int K, int NOUT>
+__device__ __forceinline__ void warp_mma_layer(const __nv_bfloat16* A, int lda,
+                                               const __nv_bfloat16* W, int ldw, float (*acc)[4]) {
+  const int lane = threadIdx.x & 31;
+  const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
+  const int brow = lane & 7, bcol = ((lane >> 3) & 1) * 8;
+#pragma unroll
+  for (int nt = 0; nt < NOUT / 8; nt++) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+  for (int kt = 0; kt < K / 16; kt++) {
+    uint32_t a[4];
+    ldsm_x4(a, A + arow * lda + kt * 16 + acol);
+#pragma unroll
+    for (int nt = 0; nt < NOUT / 8; nt++) {
+      uint32_t b[2];
+      ldsm_x2(b, W + (nt * 8 + brow) * ldw + kt * 16 + bcol);
+      mma16816(acc[nt], a, b);
     }
-    __syncthreads();
+  }
+}
+
+// out (16 x NOUT, BF16, row stride ldo) = GELU(acc + bias)
+template <int NOUT>
+__device__ __forceinline__ void store_gelu(float (*acc)[4], const float* bias, __nv_bfloat16* out,
+                                           int ldo) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < NOUT / 8; nt++) {
+    const int col = nt * 8 + 2 * t;
+    const float b0 = bias[col], b1 = bias[col + 1];
+    *reinterpret_cast<uint32_t*>(out + g * ldo + col) =
+        pack2(__float2bfloat16_rn(gelu(acc[nt][0] + b0)), __float2bfloat16_rn(gelu(acc[nt][1] + b1)));
+    *reinterpret_cast<uint32_t*>(out + (g + 8) * ldo + col) =
+        pack2(__float2bfloat16_rn(gelu(acc[nt][2] + b0)), __float2bfloat16_rn(gelu(acc[nt][3] + b1)));
+  }
+}
+
+__global__ void __launch_bounds__(kInferWarps * 32, 1)
+    k_mlp_infer(MlpDev m, const __nv_bfloat16* X, int64_t rows, float* Y, int nout) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __nv_bfloat16* w1 = reinterpret_cast<__nv_bfloat16*>(smraw);  // [kHid][kLdIn]
+  __nv_bfloat16* w2 = w1 + kHid * kLdIn;                          // [kHid][kLdHid]
+  __nv_bfloat16* w3 = w2 + kHid * kLdHid;                         // [kHid][kLdHid]
+  __nv_bfloat16* w4 = w3 + kHid * kLdHid;                         // [kOutPad][kLdHid]
+  float* sb = reinterpret_cast<float*>(w4 + kOutPad * kLdHid);    // [3 kHid + kOutPad]
+  __nv_bfloat16* tiles = reinterpret_cast<__nv_bfloat16*>(sb + 3 * kHid + kOutPad);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __nv_bfloat16* xs = tiles + warp * 16 * (kLdIn + kLdHid);  // [16][kLdIn]
+  __nv_bfloat16* act = xs + 16 * kLdIn;                       // [16][kLdHid]
+  const __nv_bfloat16* g1 = m.wbf;
+  const __nv_bfloat16* g2 = g1 + kHid * kIn;
+  const __nv_bfloat16* g3 = g2 + kHid * kHid;
+  const __nv_bfloat16* g4 = g3 + kHid * kHid;
+  for (int k = threadIdx.x; k < kHid * kIn; k += blockDim.x) w1[(k / kIn) * kLdIn + k % kIn] = g1[k];
+  for (int k = threadIdx.x; k < kHid * kHid; k += blockDim.x) {
+    w2[(k / kHid) * kLdHid + k % kHid] = g2[k];
+    w3[(k / kHid) * kLdHid + k % kHid] = g3[k];
+  }
+  for (int k = threadIdx.x; k < kOutPad * kHid; k += blockDim.x)
+    w4[(k / kHid) * kLdHid + k % kHid] = g4[k];
+  for (int k = threadIdx.x; k < 3 * kHid + kOutPad; k += blockDim.x) sb[k] = m.b[k];
+  __syncthreads();
+  float acc[kHid / 8][4];
+  const int64_t ntiles = (rows + 15) / 16;
+  for (int64_t tile = (int64_t)blockIdx.x * kInferWarps + warp; tile < ntiles;
+       tile += (int64_t)gridDim.x * kInferWarps) {
+    const int64_t r0 = tile * 16;
+    // the tile's 16 input rows, 16-byte words (X rows are 160 bytes)
+    for (int w = lane; w < 16 * (kIn / 8); w += 32) {
+      const int r = w / (kIn / 8), c = w % (kIn / 8);
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (r0 + r < rows) v = *reinterpret_cast<const uint4*>(X + (r0 + r) * kIn + c * 8);
+      *reinterpret_cast<uint4*>(xs + r * kLdIn + c * 8) = v;
+    }
+    __syncwarp();
+    warp_mma_layer<kIn, kHid>(xs, kLdIn, w1, kLdIn, acc);
+    store_gelu<kHid>(acc, sb, act, kLdHid);
+    __syncwarp();
+    warp_mma_layer<kHid, kHid>(act, kLdHid, w2, kLdHid, acc);
+    __syncwarp();  // every lane has read the tile before it is overwritten
+    store_gelu<kHid>(acc, sb + kHid, act, kLdHid);
+    __syncwarp();
+    warp_mma_layer<kHid, kHid>(act, kLdHid, w3, kLdHid, acc);
+    __syncwarp();
+    store_gelu<kHid>(acc, sb + 2 * kHid, act, kLdHid);
+    __syncwarp();
+    float y[kOutPad / 8][4];
+    warp_mma_layer<kHid, kOutPad>(act, kLdHid, w4, kLdHid, y);
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < kOutPad / 8; nt++)
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const int col = nt * 8 + 2 * t + e;
+        if (col >= nout) continue;
+        const float bo = sb[3 * kHid + col];
+        if (r0 + g < rows) Y[(r0 + g) * nout + col] = y[nt][e] + bo;
+        if (r0 + g + 8 < rows) Y[(r0 + g + 8) * nout + col] = y[nt][2 + e] + bo;
+      }
+    __syncwarp();  // the tile buffers are free for the next tile
   }
 }
 
@@ -463,14 +572,18 @@ size_t mlp_smem_grad() {
 
 cudaError_t launch_mlp_forward(const MlpDev& m, const __nv_bfloat16* X, int64_t rows, float* Y,
                                int nout, cudaStream_t s) {
-  size_t smem = mlp_smem_forward();
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((reinterpret_cast<uintptr_t>(X) & 15u) != 0u || nout > kOutPad) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(__nv_bfloat16) * (kHid * kLdIn + 2 * kHid * kLdHid + kOutPad * kLdHid +
+                                               kInferWarps * 16 * (kLdIn + kLdHid)) +
+                      sizeof(float) * (3 * kHid + kOutPad);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  int blocks = (int)std::min<int64_t>((rows + kRows - 1) / kRows, 152);
+  const int64_t ntiles = (rows + 15) / 16;
+  int blocks = (int)std::min<int64_t>((ntiles + kInferWarps - 1) / kInferWarps, 152);
   if (blocks < 1) blocks = 1;
   count_launch();
-  k_mlp_forward<<<blocks, kThreads, smem, s>>>(m, X, rows, Y, nout);
+  k_mlp_infer<<<blocks, kInferWarps * 32, smem, s>>>(m, X, rows, Y, nout);
   return cudaGetLastError();
 }
 
