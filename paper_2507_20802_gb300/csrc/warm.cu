@@ -176,6 +176,29 @@ __device__ __forceinline__ void mma16816(float* c, const uint32_t* a, const uint
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// Fragment loads for mma.m16n8k16 from shared memory (rows of 8 BF16 at
+// 16-byte aligned addresses, one address per lane): x4 gives an A fragment
+// (16 rows x 16 k), x2 a B fragment from 8 rows of W (n) with k contiguous,
+// x2.trans a B fragment from 16 rows of a k-major matrix (k rows, n contiguous).
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t* r, const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t* r, const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(a));
+}
+
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
@@ -193,6 +216,8 @@ template <int K, int NOUT>
 __device__ __forceinline__ void warp_layer(const __nv_bfloat16* A, int lda, const __nv_bfloat16* W,
                                            int ldw, const float* bias, float* z, int ldz) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
+  const int brow = lane & 7, bcol = ((lane >> 3) & 1) * 8;
 #pragma unroll
   for (int nt = 0; nt < NOUT / 8; nt++) {
     float c[4] = {0.f, 0.f, 0.f, 0.f};
@@ -200,13 +225,8 @@ __device__ __forceinline__ void warp_layer(const __nv_bfloat16* A, int lda, cons
     for (int kt = 0; kt < K / 16; kt++) {
       const int k0 = kt * 16;
       uint32_t a[4], b[2];
-      a[0] = pack2(A[g * lda + k0 + 2 * t], A[g * lda + k0 + 2 * t + 1]);
-      a[1] = pack2(A[(g + 8) * lda + k0 + 2 * t], A[(g + 8) * lda + k0 + 2 * t + 1]);
-      a[2] = pack2(A[g * lda + k0 + 2 * t + 8], A[g * lda + k0 + 2 * t + 9]);
-      a[3] = pack2(A[(g + 8) * lda + k0 + 2 * t + 8], A[(g + 8) * lda + k0 + 2 * t + 9]);
-      const __nv_bfloat16* wr = W + (nt * 8 + g) * ldw + k0;
-      b[0] = pack2(wr[2 * t], wr[2 * t + 1]);
-      b[1] = pack2(wr[2 * t + 8], wr[2 * t + 9]);
+      ldsm_x4(a, A + arow * lda + k0 + acol);
+      ldsm_x2(b, W + (nt * 8 + brow) * ldw + k0 + bcol);
       mma16816(c, a, b);
     }
     const int col = nt * 8 + 2 * t;
@@ -276,18 +296,6 @@ constexpr int kInferWarps = 16;
 constexpr int kLdIn = kIn + 8;
 constexpr int kLdHid = kHid + 8;
 
-__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-__device__ __forceinline__ void ldsm_x2(uint32_t* r, const void* p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-               : "=r"(r[0]), "=r"(r[1])
-               : "r"(a));
-}
 
 // acc[nt] = A (16 x K, BF16, row stride lda) times W^T (W: NOUT x K, row
 // stride ldw), FP32 accumulators in the mma.m16n8k16 layout
@@ -500,15 +508,36 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(MlpDev m, const __nv_bflo
       }
       __syncthreads();
       if (l > 0) {
-        // dA_{l-1}[r][i] = sum_o dZ[r][o] W_l[o][i]; then times GELU'(Z_{l-1})
+        // dA_{l-1}[r][i] = sum_o dZ[r][o] W_l[o][i] on the tensor cores (dZ
+        // in BF16, as for dW; FP32 accumulation), then times GELU'(Z_{l-1}).
+        // dZ goes row-major into the transposed-A buffer, free after dW.
         const __nv_bfloat16* Wl = W[l];
-        const float* zprev = sz + (l - 1) * kRows * kHid;
-        // each thread handles (r, i) pairs; plain FP32 dot products (small K)
-        for (int k = threadIdx.x; k < kRows * nin; k += blockDim.x) {
-          const int r = k / nin, i = k % nin;
-          float acc = 0.f;
-          for (int o = 0; o < no; o++) acc += dz[r * kHid + o] * __bfloat162float(Wl[o * nin + i]);
-          sz[(l - 1) * kRows * kHid + r * kHid + i] = acc * gelu_grad(zprev[r * kHid + i]);
+        float* zprev = sz + (l - 1) * kRows * kHid;
+        __nv_bfloat16* dzr = at;  // [kRows][no]
+        for (int k = threadIdx.x; k < kRows * no; k += blockDim.x)
+          dzr[k] = __float2bfloat16_rn(dz[(k / no) * kHid + k % no]);
+        __syncthreads();
+        {
+          const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+          const int r0 = warp * 16;
+          const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
+          const int krow = (lane & 7) + ((lane >> 3) & 1) * 8;
+          for (int nt = 0; nt < nin / 8; nt++) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int kt = 0; kt < no / 16; kt++) {
+              uint32_t a[4], b[2];
+              ldsm_x4(a, dzr + (r0 + arow) * no + kt * 16 + acol);
+              ldsm_x2_trans(b, Wl + (kt * 16 + krow) * nin + nt * 8);
+              mma16816(c, a, b);
+            }
+            const int i0 = nt * 8 + 2 * t;
+            float* z0 = zprev + (r0 + g) * kHid + i0;
+            float* z1 = zprev + (r0 + g + 8) * kHid + i0;
+            z0[0] = c[0] * gelu_grad(z0[0]);
+            z0[1] = c[1] * gelu_grad(z0[1]);
+            z1[0] = c[2] * gelu_grad(z1[0]);
+            z1[1] = c[3] * gelu_grad(z1[1]);
+          }
         }
         __syncthreads();
         for (int k = threadIdx.x; k < kRows * kHid; k += blockDim.x)
