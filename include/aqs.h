@@ -180,6 +180,12 @@ typedef struct {
                              index shows that its result will be discarded;
                              1: every chain runs to its end as in the paper.
                              Results and decisions are identical. */
+  int K_max;              /* dynamic K (the paper leaves an adaptive step count
+                             to future work, Sec. 5): with K_max > K the next
+                             pass uses min(K_max, 2 K) after a pass without a
+                             failed test and max(1, ceil(q / P)) after one, q the
+                             steps that pass accepted; <= K keeps K fixed.  The
+                             trajectory is that of sequential AQS either way. */
 } aqs_parallel_params;
 
 typedef struct {
@@ -189,6 +195,7 @@ typedef struct {
   int64_t fire_iters_total; /* FIRE iterations of all chains, rejected ones included */
   int64_t evals64_total;    /* FP64 force evaluations of all chains */
   int64_t chains_stopped;   /* chains stopped early (see run_discarded) */
+  int32_t* K_pass;          /* nullable, capacity n_steps: K of every pass */
   /* caller-allocated host arrays indexed by accepted step (nullable each),
    * capacity n_steps: */
   double* energy;

@@ -205,7 +205,8 @@ def aqs(pot, fp, x, types, H, dgamma, n_steps):
     return dict(x=x, H=H, status=st, E=E, tau=tau, iters=it, D=D)
 
 
-def parallel(pot, fp, x, types, H, dgamma, K, P, n_steps, eq_tol, n_threads=1, log_cap=100000):
+def parallel(pot, fp, x, types, H, dgamma, K, P, n_steps, eq_tol, n_threads=1, log_cap=100000,
+             K_max=0):
     x, t, H = _pos(x).copy(), _types(types), _pos(H).copy()
     E, tau, D = np.zeros(n_steps), np.zeros(n_steps), np.zeros(n_steps)
     it = np.zeros(n_steps, dtype=np.int64)
@@ -214,15 +215,17 @@ def parallel(pot, fp, x, types, H, dgamma, K, P, n_steps, eq_tol, n_threads=1, l
     le = np.zeros(log_cap, dtype=np.uint8)
     lm = np.zeros(log_cap)
     stats = ParallelStats()
+    Kp = np.zeros(max(1, n_steps), dtype=np.int32)
     st = lib().orc_parallel(C.byref(pot), C.byref(fp), x.shape[0], _p(x), _p(t, C.c_int32), _p(H),
                             C.c_double(dgamma), K, P, n_steps, C.c_double(eq_tol), n_threads,
                             _p(E), _p(tau), _p(it, C.c_int64), _p(D), _p(li, C.c_int64),
                             _p(lc, C.c_int32), _p(le, C.c_uint8), _p(lm), C.c_int64(log_cap),
-                            C.byref(stats))
+                            C.byref(stats), int(K_max), _p(Kp, C.c_int32))
     n = min(stats.n_log, log_cap)
     return dict(x=x, H=H, status=st, E=E, tau=tau, iters=it, D=D,
                 log_iter=li[:n], log_i=lc[:n], log_eq=le[:n], log_m=lm[:n],
-                iterations=stats.iterations, fire_iters_total=stats.fire_iters_total)
+                iterations=stats.iterations, fire_iters_total=stats.fire_iters_total,
+                K_pass=Kp[:stats.iterations])
 
 
 def alg1_decide(K_i, eq):

@@ -102,25 +102,28 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
                  const int32_t* types, double* H, double dgamma, int K, int P, int n_steps,
                  double eq_tol, int n_threads, double* E_k, double* tau_k, int64_t* iters_k,
                  double* D_k, int64_t* log_iter, int32_t* log_i, uint8_t* log_eq, double* log_m,
-                 int64_t log_cap, orc_parallel_stats* stats) {
+                 int64_t log_cap, orc_parallel_stats* stats, int K_max, int32_t* K_pass) {
   if (K < 1 || P < 1 || n_steps < 0) return ORC_ERR_INVALID_ARG;
+  const int Kcap = K_max > K ? K_max : K; /* longest chain any pass can have */
+  const int adaptive = K_max > K;
   int dim = pot->dim;
   size_t nd = (size_t)n * dim;
   double* xs = malloc(nd * sizeof(double) * P);   /* chain states */
   double* xo = malloc(nd * sizeof(double) * P);   /* outgoing configurations */
   double* Hs = malloc(sizeof(double) * 9 * P);
-  double* cE = malloc(sizeof(double) * (size_t)K * P);
-  double* cT = malloc(sizeof(double) * (size_t)K * P);
-  double* cD = malloc(sizeof(double) * (size_t)K * P);
-  int64_t* cI = malloc(sizeof(int64_t) * (size_t)K * P);
+  double* cE = malloc(sizeof(double) * (size_t)Kcap * P);
+  double* cT = malloc(sizeof(double) * (size_t)Kcap * P);
+  double* cD = malloc(sizeof(double) * (size_t)Kcap * P);
+  int64_t* cI = malloc(sizeof(int64_t) * (size_t)Kcap * P);
   chain_job* jobs = malloc(sizeof(chain_job) * P);
   pthread_t* th = malloc(sizeof(pthread_t) * P);
   int32_t* Ki = malloc(sizeof(int32_t) * P);
   uint8_t* eq = calloc(P, 1);
   int64_t n_cur = 0, iter = 0, n_log = 0, fire_total = 0;
   int status = ORC_OK;
-  double dgc = K * dgamma; /* coarse increment dgamma^c = K dgamma */
   while (n_cur < n_steps) {
+    double dgc = K * dgamma; /* coarse increment dgamma^c = K dgamma of this pass */
+    if (K_pass) K_pass[iter] = K;
     int64_t rem = n_steps - n_cur;
     int P_eff = (int)((rem + K - 1) / K);
     if (P_eff > P) P_eff = P;
@@ -134,8 +137,8 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
       chain_job* c = &jobs[i];
       c->pot = pot; c->fp = fp; c->n = n; c->types = types; c->dgamma = dgamma;
       c->K_i = Ki[i]; c->x = xs + i * nd; c->H = Hs + 9 * i; c->x_out = xo + i * nd;
-      c->E = cE + (size_t)i * K; c->tau = cT + (size_t)i * K; c->D = cD + (size_t)i * K;
-      c->iters = cI + (size_t)i * K;
+      c->E = cE + (size_t)i * Kcap; c->tau = cT + (size_t)i * Kcap;
+      c->D = cD + (size_t)i * Kcap; c->iters = cI + (size_t)i * Kcap;
     }
     /* level II: P chains (Sec. 3.3, Eq. 19; Algorithm 1 parallel loop) */
     if (n_threads > 1) {
@@ -173,16 +176,22 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
     int64_t k = n_cur;
     for (int i = 0; i <= last; i++)
       for (int s = 0; s < Ki[i]; s++, k++) {
-        if (E_k) E_k[k] = cE[(size_t)i * K + s];
-        if (tau_k) tau_k[k] = cT[(size_t)i * K + s];
-        if (iters_k) iters_k[k] = cI[(size_t)i * K + s];
-        if (D_k) D_k[k] = cD[(size_t)i * K + s];
+        if (E_k) E_k[k] = cE[(size_t)i * Kcap + s];
+        if (tau_k) tau_k[k] = cT[(size_t)i * Kcap + s];
+        if (iters_k) iters_k[k] = cI[(size_t)i * Kcap + s];
+        if (D_k) D_k[k] = cD[(size_t)i * Kcap + s];
       }
     /* r_star <- r_q (end of chain `last`), H follows */
     memcpy(x, xs + (size_t)last * nd, nd * sizeof(double));
     memcpy(H, Hs + 9 * last, sizeof(double) * dim * dim);
     n_cur += q;
     iter++;
+    if (adaptive) {
+      /* dynamic K: longer chains after a clean pass, after a failed test
+       * chains that together span the distance this pass advanced */
+      if (first_fail < 0) K = 2 * K < Kcap ? 2 * K : Kcap;
+      else K = (int)((q + P - 1) / P) > 1 ? (int)((q + P - 1) / P) : 1;
+    }
   }
   if (stats) {
     stats->iterations = iter;

@@ -123,11 +123,18 @@ typedef struct {
  * log_iter = while-loop pass, log_i = chain index i, log_eq = 1 if equal,
  * log_m = measured max displacement.  n_threads > 1 runs the level-II
  * chains on that many POSIX threads (the paper's design). */
+/* Dynamic K (the paper names an adaptive step count as future work, Sec. 5;
+ * this rule is a reading): with K_max > K, the chain length of the next pass
+ * is min(K_max, 2 K) after a pass without a failed test and
+ * max(1, ceil(q / P)) after a failed test, q the steps that pass accepted.
+ * K_max <= K keeps K fixed.  K_pass (nullable, capacity n_steps) receives the
+ * K of every pass.  Any K schedule reproduces sequential AQS (Algorithm 1 is
+ * exact), which the tests use as the pin. */
 int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, double* x,
                  const int32_t* types, double* H, double dgamma, int K, int P, int n_steps,
                  double eq_tol, int n_threads, double* E_k, double* tau_k, int64_t* iters_k,
                  double* D_k, int64_t* log_iter, int32_t* log_i, uint8_t* log_eq, double* log_m,
-                 int64_t log_cap, orc_parallel_stats* stats);
+                 int64_t log_cap, orc_parallel_stats* stats, int K_max, int32_t* K_pass);
 
 /* Pure decision rule of Algorithm 1 (lines after the level-II loop): given
  * the chain lengths K_i (i = 0..P_eff-1) and the equality outcomes eq[i] for

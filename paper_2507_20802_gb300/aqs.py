@@ -60,13 +60,14 @@ class aqs_parallel_params(C.Structure):
     _fields_ = [("dgamma", C.c_double), ("K", C.c_int), ("P", C.c_int),
                 ("n_steps", C.c_int64), ("eq_tol", C.c_double),
                 ("event_threshold", C.c_double), ("max_iterations", C.c_int64),
-                ("warm_start", C.c_int), ("run_discarded", C.c_int)]
+                ("warm_start", C.c_int), ("run_discarded", C.c_int), ("K_max", C.c_int)]
 
 
 class aqs_parallel_result(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("accepted_steps", C.c_int64),
                 ("rejections", C.c_int64), ("fire_iters_total", C.c_int64),
                 ("evals64_total", C.c_int64), ("chains_stopped", C.c_int64),
+                ("K_pass", C.POINTER(C.c_int32)),
                 ("energy", C.POINTER(C.c_double)), ("tau", C.POINTER(C.c_double)),
                 ("fire_iters", C.POINTER(C.c_int64)), ("nonaffine", C.POINTER(C.c_double)),
                 ("event", C.POINTER(C.c_uint8)),
@@ -249,10 +250,10 @@ def aqs_run_sequential(h, fire, dgamma, n_steps, n_replicas):
 
 def aqs_parallel_step(h, replica, fire, dgamma, K, P, n_steps, eq_tol=1e-6,
                       event_threshold=1e-2, max_iterations=0, warm_start=0, log_cap=100000,
-                      run_discarded=0):
+                      run_discarded=0, K_max=0):
     p = aqs_parallel_params(dgamma=dgamma, K=K, P=P, n_steps=n_steps, eq_tol=eq_tol,
                             event_threshold=event_threshold, max_iterations=max_iterations,
-                            warm_start=warm_start, run_discarded=run_discarded)
+                            warm_start=warm_start, run_discarded=run_discarded, K_max=K_max)
     n = max(int(n_steps), 1)
     E, tau, D = np.zeros(n), np.zeros(n), np.zeros(n)
     it = np.zeros(n, dtype=np.int64)
@@ -270,13 +271,15 @@ def aqs_parallel_step(h, replica, fire, dgamma, K, P, n_steps, eq_tol=1e-6,
     r.log_i = lc.ctypes.data_as(C.POINTER(C.c_int32))
     r.log_eq = le.ctypes.data_as(C.POINTER(C.c_uint8))
     r.log_m = _dp(lm)
+    kp = np.zeros(n, dtype=np.int32)
+    r.K_pass = kp.ctypes.data_as(C.POINTER(C.c_int32))
     check(lib().aqs_parallel_step(h, replica, C.byref(fire), C.byref(p), C.byref(r)))
     k = r.accepted_steps
     nl = min(r.n_log, log_cap)
     return dict(E=E[:k], tau=tau[:k], iters=it[:k], D=D[:k], event=ev[:k],
                 iterations=r.iterations, accepted=r.accepted_steps, rejections=r.rejections,
                 fire_iters_total=r.fire_iters_total, evals64_total=r.evals64_total,
-                chains_stopped=r.chains_stopped, log_iter=li[:nl], log_i=lc[:nl], log_eq=le[:nl], log_m=lm[:nl])
+                chains_stopped=r.chains_stopped, K_pass=kp[:r.iterations], log_iter=li[:nl], log_i=lc[:nl], log_eq=le[:nl], log_m=lm[:nl])
 
 
 def aqs_compare_configs(ha, ra, hb, rb, tol):

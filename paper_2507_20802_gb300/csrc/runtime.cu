@@ -1193,7 +1193,13 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
   if (p->warm_start) return fail(AQS_ERR_UNSUPPORTED, "warm start is not available");
   const double eq_tol = p->eq_tol > 0.0 ? p->eq_tol : 1e-6;
   const double ev_thr = p->event_threshold > 0.0 ? p->event_threshold : 1e-2;
-  const int K = p->K, P = p->P, D = s->dim;
+  const int P = p->P, D = s->dim;
+  // dynamic K (K_max > K): the chain length of the next pass is doubled after
+  // a pass without a failed test, up to K_max, and ceil(q / P) after a failed
+  // test, q the steps the pass accepted (the same rule as the oracle's)
+  const bool adaptive = p->K_max > p->K;
+  const int Kcap = adaptive ? p->K_max : p->K;
+  int K = p->K;
   const int n = (int)s->n[src];
   AQS_TRY(ensure_chains(s, src, P));
   aqs_system* c = s->chains;
@@ -1201,12 +1207,13 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
   out->fire_iters_total = out->evals64_total = 0;
   out->chains_stopped = 0;
   out->n_log = 0;
-  std::vector<double> cE((size_t)P * K), cT((size_t)P * K), cD((size_t)P * K);
-  std::vector<int64_t> cI((size_t)P * K);
+  std::vector<double> cE((size_t)P * Kcap), cT((size_t)P * Kcap), cD((size_t)P * Kcap);
+  std::vector<int64_t> cI((size_t)P * Kcap);
   int64_t n_cur = 0;
   const size_t per = (size_t)D * n;
   while (n_cur < p->n_steps && (p->max_iterations <= 0 || out->iterations < p->max_iterations)) {
     const int64_t rem = p->n_steps - n_cur;
+    if (out->K_pass && out->iterations < p->n_steps) out->K_pass[out->iterations] = K;
     const int P_eff = (int)std::min<int64_t>(P, (rem + K - 1) / K);
     std::vector<int> Ki(P_eff, K);
     if (rem < (int64_t)P_eff * K) Ki[P_eff - 1] = (int)(rem - (int64_t)(P_eff - 1) * K);
@@ -1303,10 +1310,10 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
       }
       for (int k = 0; k < Ki[i] && k + 1 < done; k++) {
         const double* q = rec + (size_t)(k + 1) * kRecFields;
-        cE[(size_t)i * K + k] = q[0];
-        cT[(size_t)i * K + k] = q[1];
-        cD[(size_t)i * K + k] = q[2];
-        cI[(size_t)i * K + k] = (int64_t)q[3];
+        cE[(size_t)i * Kcap + k] = q[0];
+        cT[(size_t)i * Kcap + k] = q[1];
+        cD[(size_t)i * Kcap + k] = q[2];
+        cI[(size_t)i * Kcap + k] = (int64_t)q[3];
         out->fire_iters_total += (int64_t)q[3];
         out->evals64_total += (int64_t)q[4];
       }
@@ -1335,7 +1342,7 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
     int64_t kk = n_cur;
     for (int i = 0; i <= last; i++)
       for (int j = 0; j < Ki[i]; j++, kk++) {
-        size_t src_i = (size_t)i * K + j;
+        size_t src_i = (size_t)i * Kcap + j;
         if (out->energy) out->energy[kk] = cE[src_i];
         if (out->tau) out->tau[kk] = cT[src_i];
         if (out->fire_iters) out->fire_iters[kk] = cI[src_i];
@@ -1348,6 +1355,9 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
     out->accepted_steps += q;
     out->iterations++;
     if (first_fail >= 0) out->rejections++;
+    if (adaptive)
+      K = first_fail < 0 ? std::min(Kcap, 2 * K)
+                         : (int)std::max<int64_t>(1, (q + P - 1) / P);
   }
   return AQS_OK;
 }

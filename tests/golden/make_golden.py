@@ -12,6 +12,8 @@ Each file is an .npz of FP64/int arrays:
 * par_2d_n256_s<seed>.npz -- Algorithm 1 from that glass at the paper's
   increment dgamma = 1/200 (Sec. 4) with K = 3, P = 4, 30 steps: per-step
   observables, decision log, final positions.
+* pardynk_2d_n256_s0.npz -- the same Algorithm-1 run with dynamic K
+  (K_max = 12): chain length per pass, decisions, observables.
 * aqs_3d_n2048_s0.npz -- three sequential AQS steps of the 3D glass,
   dgamma = 5e-5.
 * glass_sl_n400_s0.npz, aqs_sl_n400_s0.npz -- the paper's S/L glass (N = 400,
@@ -79,6 +81,16 @@ def job_par2d256():
     assert r["status"] == 0
     np.savez(os.path.join(HERE, "par_2d_n256_s0.npz"), dgamma=dg, K=K, P=P, n_steps=n,
              eq_tol=1e-6, **r)
+
+
+def job_pardynk2d256():
+    g = glass(2, 256, 0)
+    dg, K, P, n, K_max = 5e-3, 3, 4, 30, 12
+    r = oracle.parallel(_pot(2), _fire(), g["x"], g["types"], g["H"], dg, K, P, n, eq_tol=1e-6,
+                        n_threads=4, K_max=K_max)
+    assert r["status"] == 0
+    np.savez(os.path.join(HERE, "pardynk_2d_n256_s0.npz"), dgamma=dg, K=K, P=P, n_steps=n,
+             K_max=K_max, eq_tol=1e-6, **r)
 
 
 def job_aqs3d2048():

@@ -379,3 +379,25 @@ def test_paper_sl_glass_trajectory_matches_golden(A, syn, prec):
     np.testing.assert_allclose(out["D"][:, 0], gold["D"], rtol=1e-4)
     assert mi_disp(s.positions(), gold["x"], gold["H"]) < 1e-6
     np.testing.assert_allclose(s.box(), gold["H"], rtol=1e-12)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_dynamic_k_matches_golden(A, syn, glass256, prec):
+    """Algorithm 1 with dynamic K (K = 3, K_max = 12, P = 4, dgamma = 1/200,
+    30 steps): the chain length of every pass, the decision log and the
+    trajectory of the stored oracle run."""
+    gold = load_golden("pardynk_2d_n256_s0.npz")
+    x, t, H = glass256["x"], glass256["types"], glass256["H"]
+    P = A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED
+    s = make_system(A, syn, x, t, H, P)
+    r = s.parallel_step(float(gold["dgamma"]), int(gold["K"]), int(gold["P"]),
+                        int(gold["n_steps"]), eq_tol=float(gold["eq_tol"]),
+                        K_max=int(gold["K_max"]))
+    assert np.array_equal(r["K_pass"], gold["K_pass"])
+    for key in ("log_i", "log_eq", "log_iter"):
+        assert np.array_equal(r[key], gold[key]), key
+    assert r["iterations"] == int(gold["iterations"])
+    rel = 1e-9 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(r["E"], gold["E"], rtol=rel)
+    assert np.array_equal(r["D"] > EV_THR, gold["D"] > EV_THR)
+    assert mi_disp(s.positions(), gold["x"], gold["H"]) < 1e-6

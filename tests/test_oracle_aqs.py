@@ -84,3 +84,50 @@ def test_sequential_aqs_elastic_step_is_small(orc, small_glass):
     # non-affine response is linear in the increment for an elastic step
     r2 = orc.aqs(pot, fp, x0, t, H, 2e-5, 1)
     assert r2["D"][0] == pytest.approx(2 * r["D"][0], rel=0.05)
+
+
+def _check_k_rule(par, K0, K_max, P):
+    """The recorded chain length of every pass follows the dynamic-K rule."""
+    Ks = list(par["K_pass"])
+    assert Ks[0] == K0
+    for p in range(1, len(Ks)):
+        sel = par["log_iter"] == p - 1
+        fails = par["log_i"][sel][par["log_eq"][sel] == 0]
+        if len(fails) == 0:
+            assert Ks[p] == min(K_max, 2 * Ks[p - 1]), (p, Ks)
+        else:
+            q = int(fails[0]) * Ks[p - 1]  # chains 0..i-1 accepted (none shortened here)
+            assert Ks[p] == max(1, -(-q // P)), (p, Ks, q)
+
+
+def test_dynamic_k_keeps_the_sequential_trajectory(orc, small_glass):
+    """Any chain-length schedule reproduces sequential AQS (Algorithm 1 is
+    exact); with rejections the schedule shrinks and grows by the rule."""
+    pot, fp, x0, t, H = small_glass
+    dg, K, P, n = 5e-3, 3, 4, 30
+    seq = orc.aqs(pot, fp, x0, t, H, dg, n)
+    par = orc.parallel(pot, fp, x0, t, H, dg, K, P, n, eq_tol=1e-6, K_max=12)
+    assert par["status"] == 0
+    np.testing.assert_allclose(par["E"], seq["E"], rtol=1e-9)
+    assert orc.max_rel_disp(par["x"], seq["x"], seq["H"]) < 1e-6
+    assert np.array_equal(par["D"] > 1e-2, seq["D"] > 1e-2)
+    assert np.any(par["log_eq"] == 0)
+    # all but the last pass are full windows, so the rule can be checked exactly
+    full = dict(par)
+    full["K_pass"] = par["K_pass"][:-1]
+    _check_k_rule(full, K, 12, P)
+    # K_max <= K is the fixed schedule
+    fixed = orc.parallel(pot, fp, x0, t, H, dg, K, P, n, eq_tol=1e-6, K_max=K)
+    ref = orc.parallel(pot, fp, x0, t, H, dg, K, P, n, eq_tol=1e-6)
+    assert np.array_equal(fixed["E"], ref["E"]) and np.all(fixed["K_pass"] == K)
+
+
+def test_dynamic_k_doubles_on_the_lattice(orc, syn):
+    """No plastic events on the lattice: K doubles every pass up to K_max."""
+    pot = orc.make_potential(2, syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR)
+    fp = orc.make_fire(**syn.FIRE)
+    x, t, H = syn.triangular_lattice(8, 8)
+    par = orc.parallel(pot, fp, x, t, H, 1e-3, 1, 2, 40, eq_tol=1e-6, K_max=8)
+    assert par["status"] == 0
+    assert list(par["K_pass"]) == [1, 2, 4, 8, 8, 8][:len(par["K_pass"])]
+    assert par["H"][0, 1] == pytest.approx(40 * 1e-3 * H[1, 1], rel=1e-12)
