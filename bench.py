@@ -478,6 +478,8 @@ def main():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--baseline-steps", type=int, default=2)
     ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d", "warm"], default="cfg1")
+    ap.add_argument("--k-max", type=int, default=0,
+                    help="> K: dynamic K up to this chain length (default: fixed K = 10)")
     ap.add_argument("--seeds", type=int, default=0,
                     help="> 0: Metric 1 over glasses of seeds 0..n-1 (mean and std)")
     ap.add_argument("--launch-budget", type=int, default=2048,
@@ -529,11 +531,15 @@ def main():
     done = 0
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    k_cur = [K_FINE]  # chain length of the next pass (changes only with --k-max)
+
     def one_pass():
         nonlocal done
         remaining = n_total - done if n_total > done else P_CHAINS * K_FINE
         torch.cuda.nvtx.range_push("aqs_pass")  # lets a profiler select the passes
-        r = s.parallel_step(DGAMMA, K_FINE, P_CHAINS, remaining, fire=fire, max_iterations=1)
+        r = s.parallel_step(DGAMMA, k_cur[0], P_CHAINS, remaining, fire=fire, max_iterations=1,
+                            K_max=args.k_max)
+        k_cur[0] = r["K_next"]
         torch.cuda.nvtx.range_pop()
         done += r["accepted"]
         return r
@@ -671,7 +677,7 @@ def main():
                 "fp64_sequential_gpu_baseline": base,
                 "detail": {"accepted_steps": int(total_steps), "rejections": rej,
                            "chains_stopped_early": stopped, "autotune_iters": args.autotune,
-                           "launch_budget": args.launch_budget,
+                           "launch_budget": args.launch_budget, "k_max": args.k_max,
                            "wall_s": wall, "fire_iters_per_step": mean_iters,
                            "fp32_evals": st["evals32"], "fp64_evals": st["evals64"],
                            "rebuilds_in_kernel": st["rebuilds"],

@@ -196,6 +196,8 @@ typedef struct {
   int64_t evals64_total;    /* FP64 force evaluations of all chains */
   int64_t chains_stopped;   /* chains stopped early (see run_discarded) */
   int32_t* K_pass;          /* nullable, capacity n_steps: K of every pass */
+  int32_t K_next;           /* K the next pass would use (dynamic K; pass it as
+                               K to continue pass by pass) */
   /* caller-allocated host arrays indexed by accepted step (nullable each),
    * capacity n_steps: */
   double* energy;

@@ -67,7 +67,7 @@ class aqs_parallel_result(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("accepted_steps", C.c_int64),
                 ("rejections", C.c_int64), ("fire_iters_total", C.c_int64),
                 ("evals64_total", C.c_int64), ("chains_stopped", C.c_int64),
-                ("K_pass", C.POINTER(C.c_int32)),
+                ("K_pass", C.POINTER(C.c_int32)), ("K_next", C.c_int32),
                 ("energy", C.POINTER(C.c_double)), ("tau", C.POINTER(C.c_double)),
                 ("fire_iters", C.POINTER(C.c_int64)), ("nonaffine", C.POINTER(C.c_double)),
                 ("event", C.POINTER(C.c_uint8)),
@@ -279,7 +279,8 @@ def aqs_parallel_step(h, replica, fire, dgamma, K, P, n_steps, eq_tol=1e-6,
     return dict(E=E[:k], tau=tau[:k], iters=it[:k], D=D[:k], event=ev[:k],
                 iterations=r.iterations, accepted=r.accepted_steps, rejections=r.rejections,
                 fire_iters_total=r.fire_iters_total, evals64_total=r.evals64_total,
-                chains_stopped=r.chains_stopped, K_pass=kp[:r.iterations], log_iter=li[:nl], log_i=lc[:nl], log_eq=le[:nl], log_m=lm[:nl])
+                chains_stopped=r.chains_stopped, K_pass=kp[:r.iterations], K_next=r.K_next,
+                log_iter=li[:nl], log_i=lc[:nl], log_eq=le[:nl], log_m=lm[:nl])
 
 
 def aqs_compare_configs(ha, ra, hb, rb, tol):

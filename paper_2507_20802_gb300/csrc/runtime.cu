@@ -1206,6 +1206,7 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
   out->iterations = out->accepted_steps = out->rejections = 0;
   out->fire_iters_total = out->evals64_total = 0;
   out->chains_stopped = 0;
+  out->K_next = p->K;
   out->n_log = 0;
   std::vector<double> cE((size_t)P * Kcap), cT((size_t)P * Kcap), cD((size_t)P * Kcap);
   std::vector<int64_t> cI((size_t)P * Kcap);
@@ -1359,6 +1360,7 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
       K = first_fail < 0 ? std::min(Kcap, 2 * K)
                          : (int)std::max<int64_t>(1, (q + P - 1) / P);
   }
+  out->K_next = K;
   return AQS_OK;
 }
 
