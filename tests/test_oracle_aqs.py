@@ -3,10 +3,10 @@ against the properties the paper proves or states (no GPU):
 
 * the decision rule reproduces the worked 15-step, 3-thread example (Sec. 3.5);
 * the parallel trajectory equals the sequential one at every accepted step
-  (Sec. 3.6, Sec. 4: "all final configurations were equal");
+  (Sec. 3.6; the paper's runs in Sec. 4 ended in identical configurations);
 * finite termination within ceil(N_steps / K) passes, and the best case of
   ceil(N_steps / (P K)) passes when every prediction is right (Sec. 3.7);
-* repeating a run gives exactly the same outcome (Sec. 3.6), with or without
+* a repeated run gives an identical result (Sec. 3.6), with or without
   threads.
 """
 import math
