@@ -47,14 +47,6 @@ struct Coef32 {
 };
 __device__ __forceinline__ Coef32 coef32(const PairCoef& c) { return Coef32{c.Af, c.Bf, c.Cf, c.rc2f}; }
 
-// phi(s) in FP32
-__device__ __forceinline__ float phi32(const Coef32& c, float s) {
-  float a = rsqrtf(s);
-  float u = a * a;
-  float u2 = u * u, u4 = u2 * u2, u7 = u4 * u2 * u;
-  return fmaf(c.Af, u7, fmaf(c.Bf, u4, c.Cf * a));
-}
-
 // Force change of one pair between the reference separation d0 and d0 + e,
 // in FP32, by divided differences (no cancellation between phi(s) and
 // phi(s0)).  With u = 1/s, w = 1/s0, ds = s - s0:
