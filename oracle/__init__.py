@@ -205,8 +205,14 @@ def aqs(pot, fp, x, types, H, dgamma, n_steps):
     return dict(x=x, H=H, status=st, E=E, tau=tau, iters=it, D=D)
 
 
+def wrap(x, H):
+    x, H = _pos(x).copy(), _pos(H)
+    lib().orc_wrap(H.shape[0], x.shape[0], _p(x), _p(H))
+    return x
+
+
 def parallel(pot, fp, x, types, H, dgamma, K, P, n_steps, eq_tol, n_threads=1, log_cap=100000,
-             K_max=0):
+             K_max=0, wrap_ends=False):
     x, t, H = _pos(x).copy(), _types(types), _pos(H).copy()
     E, tau, D = np.zeros(n_steps), np.zeros(n_steps), np.zeros(n_steps)
     it = np.zeros(n_steps, dtype=np.int64)
@@ -220,7 +226,7 @@ def parallel(pot, fp, x, types, H, dgamma, K, P, n_steps, eq_tol, n_threads=1, l
                             C.c_double(dgamma), K, P, n_steps, C.c_double(eq_tol), n_threads,
                             _p(E), _p(tau), _p(it, C.c_int64), _p(D), _p(li, C.c_int64),
                             _p(lc, C.c_int32), _p(le, C.c_uint8), _p(lm), C.c_int64(log_cap),
-                            C.byref(stats), int(K_max), _p(Kp, C.c_int32))
+                            C.byref(stats), int(K_max), _p(Kp, C.c_int32), int(bool(wrap_ends)))
     n = min(stats.n_log, log_cap)
     return dict(x=x, H=H, status=st, E=E, tau=tau, iters=it, D=D,
                 log_iter=li[:n], log_i=lc[:n], log_eq=le[:n], log_m=lm[:n],

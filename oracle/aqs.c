@@ -102,7 +102,8 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
                  const int32_t* types, double* H, double dgamma, int K, int P, int n_steps,
                  double eq_tol, int n_threads, double* E_k, double* tau_k, int64_t* iters_k,
                  double* D_k, int64_t* log_iter, int32_t* log_i, uint8_t* log_eq, double* log_m,
-                 int64_t log_cap, orc_parallel_stats* stats, int K_max, int32_t* K_pass) {
+                 int64_t log_cap, orc_parallel_stats* stats, int K_max, int32_t* K_pass,
+                 int wrap_ends) {
   if (K < 1 || P < 1 || n_steps < 0) return ORC_ERR_INVALID_ARG;
   const int Kcap = K_max > K ? K_max : K; /* longest chain any pass can have */
   const int adaptive = K_max > K;
@@ -110,7 +111,8 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
   size_t nd = (size_t)n * dim;
   double* xs = malloc(nd * sizeof(double) * P);   /* chain states */
   double* xo = malloc(nd * sizeof(double) * P);   /* outgoing configurations */
-  double* Hs = malloc(sizeof(double) * 9 * P);
+  double* Hs = malloc(sizeof(double) * 9 * P);  /* chain cells, sheared along the chain */
+  double* H1 = malloc(sizeof(double) * 9 * P);  /* level-I cells: chain i starts at i dgamma^c */
   double* cE = malloc(sizeof(double) * (size_t)Kcap * P);
   double* cT = malloc(sizeof(double) * (size_t)Kcap * P);
   double* cD = malloc(sizeof(double) * (size_t)Kcap * P);
@@ -134,6 +136,7 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
       memcpy(xs + i * nd, x, nd * sizeof(double));
       memcpy(Hs + 9 * i, H, sizeof(double) * dim * dim);
       orc_affine_shear(dim, n, xs + i * nd, Hs + 9 * i, i * dgc);
+      memcpy(H1 + 9 * i, Hs + 9 * i, sizeof(double) * dim * dim);
       chain_job* c = &jobs[i];
       c->pot = pot; c->fp = fp; c->n = n; c->types = types; c->dgamma = dgamma;
       c->K_i = Ki[i]; c->x = xs + i * nd; c->H = Hs + 9 * i; c->x_out = xo + i * nd;
@@ -155,11 +158,15 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
       if (jobs[i].status != ORC_OK) status = jobs[i].status;
     }
     if (status != ORC_OK) break;
+    if (wrap_ends)
+      for (int i = 0; i < P_eff; i++) orc_wrap(dim, n, xs + (size_t)i * nd, Hs + 9 * i);
     /* sequential equality check (Sec. 3.4, Eq. 20): incoming r_iK | r^c_(i-1)K
-     * is the end of chain i-1, outgoing r_iK | r^c_iK is F(r^c_iK) */
+     * is the end of chain i-1, outgoing r_iK | r^c_iK is F(r^c_iK); both sit
+     * at the strain i dgamma^c, so the minimum image uses chain i's level-I
+     * cell (chain i's own cell has moved on by K_i fine steps) */
     int32_t first_fail = -1;
     for (int i = 1; i < P_eff; i++) {
-      double m = orc_max_rel_disp(dim, n, xs + (size_t)(i - 1) * nd, xo + (size_t)i * nd, Hs + 9 * i);
+      double m = orc_max_rel_disp(dim, n, xs + (size_t)(i - 1) * nd, xo + (size_t)i * nd, H1 + 9 * i);
       eq[i] = m < eq_tol;
       if (n_log < log_cap) {
         if (log_iter) log_iter[n_log] = iter;
@@ -198,7 +205,7 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
     stats->fire_iters_total = fire_total;
     stats->n_log = n_log;
   }
-  free(xs); free(xo); free(Hs); free(cE); free(cT); free(cD); free(cI);
+  free(xs); free(xo); free(Hs); free(H1); free(cE); free(cT); free(cD); free(cI);
   free(jobs); free(th); free(Ki); free(eq);
   return status;
 }

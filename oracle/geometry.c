@@ -84,6 +84,22 @@ void orc_affine_shear(int dim, int n, double* x, double* H, double dgamma) {
   orc_affine_map(dim, n, x, H, F);
 }
 
+void orc_wrap(int dim, int n, double* x, const double* H) {
+  /* fractional coordinates s = H^-1 r by back substitution (H upper
+   * triangular), then r <- r - H floor(s) */
+  for (int i = 0; i < n; i++) {
+    double s[3], m[3];
+    for (int c = dim - 1; c >= 0; c--) {
+      double t = x[i * dim + c];
+      for (int k = c + 1; k < dim; k++) t -= H[c * dim + k] * s[k];
+      s[c] = t / H[c * dim + c];
+    }
+    for (int c = 0; c < dim; c++) m[c] = floor(s[c]);
+    for (int a = 0; a < dim; a++)
+      for (int c = a; c < dim; c++) x[i * dim + a] -= H[a * dim + c] * m[c];
+  }
+}
+
 double orc_max_rel_disp(int dim, int n, const double* a, const double* b, const double* H) {
   /* u_i = mi(a_i - b_i); the minimum is degenerate under a uniform
    * translation, so the mean of u is removed before taking the largest norm. */

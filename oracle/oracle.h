@@ -70,6 +70,9 @@ double orc_half_min_width(int dim, const double* H);
 /* simple-shear affine map F^(dgamma) (Eq. 16): r_i <- F r_i for all atoms
  * (Eq. 3) and H <- F H (Eq. 1) */
 void orc_affine_shear(int dim, int n, double* x, double* H, double dgamma);
+/* maps every atom into the cell, r <- r - H floor(H^-1 r) (by whole lattice
+ * vectors; the configuration is unchanged under periodic boundaries) */
+void orc_wrap(int dim, int n, double* x, const double* H);
 /* general affine map with a d x d matrix F (row-major): r_i <- F r_i, H <- F H */
 void orc_affine_map(int dim, int n, double* x, double* H, const double* F);
 
@@ -129,12 +132,17 @@ typedef struct {
  * max(1, ceil(q / P)) after a failed test, q the steps that pass accepted.
  * K_max <= K keeps K fixed.  K_pass (nullable, capacity n_steps) receives the
  * K of every pass.  Any K schedule reproduces sequential AQS (Algorithm 1 is
- * exact), which the tests use as the pin. */
+ * exact), which the tests use as the pin.
+ * wrap_ends = 1 maps every chain's end into its cell (orc_wrap) before the
+ * equality tests.  Positions are only defined up to lattice vectors, so the
+ * decisions and the trajectory must not change; the tests use it to check
+ * that the tests are made at the shared strain's cell. */
 int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, double* x,
                  const int32_t* types, double* H, double dgamma, int K, int P, int n_steps,
                  double eq_tol, int n_threads, double* E_k, double* tau_k, int64_t* iters_k,
                  double* D_k, int64_t* log_iter, int32_t* log_i, uint8_t* log_eq, double* log_m,
-                 int64_t log_cap, orc_parallel_stats* stats, int K_max, int32_t* K_pass);
+                 int64_t log_cap, orc_parallel_stats* stats, int K_max, int32_t* K_pass,
+                 int wrap_ends);
 
 /* Pure decision rule of Algorithm 1 (lines after the level-II loop): given
  * the chain lengths K_i (i = 0..P_eff-1) and the equality outcomes eq[i] for

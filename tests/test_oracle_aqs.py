@@ -131,3 +131,71 @@ def test_dynamic_k_doubles_on_the_lattice(orc, syn):
     assert par["status"] == 0
     assert list(par["K_pass"]) == [1, 2, 4, 8, 8, 8][:len(par["K_pass"])]
     assert par["H"][0, 1] == pytest.approx(40 * 1e-3 * H[1, 1], rel=1e-12)
+
+
+def test_lattice_steps_have_zero_nonaffine_displacement(orc, syn):
+    """Every atom of the perfect triangular lattice is an inversion centre, so
+    the sheared lattice is again a minimum: the minimiser does not move and
+    D_k, measured against the affinely mapped previous minimum F r_{k-1}, is
+    zero at every step.  Measured against r_{k-1} instead, D_k would be about
+    dgamma L_y / 2 (7e-3 here)."""
+    pot = orc.make_potential(2, syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR)
+    fp = orc.make_fire(**syn.FIRE)
+    x, t, H = syn.triangular_lattice(8, 8)
+    r = orc.aqs(pot, fp, x, t, H, 2e-3, 10)
+    assert r["status"] == 0
+    assert np.all(r["iters"] == 0)
+    assert np.all(r["D"] < 1e-12), r["D"]
+
+
+def test_equality_test_uses_the_shared_strain_cell(orc, syn):
+    """Incoming and outgoing minima of a test are compared at their common
+    strain i K dgamma (Sec. 3.4), so the minimum image must use that cell.
+    With chain ends wrapped into the cell, an atom that crossed the y face
+    carries the tilt of that strain; in a later cell the image would be off by
+    K dgamma L_y.  On the lattice every prediction is right (Sec. 3.7), with
+    or without wrapping."""
+    pot = orc.make_potential(2, syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR)
+    fp = orc.make_fire(**syn.FIRE)
+    x, t, H = syn.triangular_lattice(8, 8)
+    x = x + np.array([0.0, 0.5 * H[1, 1]])  # half of the atoms outside the cell in y
+    K, P, n = 2, 3, 13
+    for wrap in (False, True):
+        par = orc.parallel(pot, fp, x, t, H, 1e-3, K, P, n, eq_tol=1e-6, wrap_ends=wrap)
+        assert par["status"] == 0
+        assert np.all(par["log_eq"] == 1) and np.all(par["log_m"] < 1e-12), par["log_m"]
+        assert par["iterations"] == math.ceil(n / (P * K))
+    # the same comparison made directly: a wrapped copy is equal in its own
+    # cell and unequal in the cell K steps later
+    xa, Ha = orc.affine_shear(x, H, K * 1e-3)
+    xw = orc.wrap(xa, Ha)
+    assert orc.max_rel_disp(xw, xa, Ha) < 1e-12
+    _, Hb = orc.affine_shear(xa, Ha, K * 1e-3)
+    assert orc.max_rel_disp(xw, xa, Hb) > 1e-3
+
+
+def test_wrapped_chain_ends_keep_decisions_on_a_glass(orc, small_glass):
+    """Wrapping chain ends (positions are defined modulo the cell) changes no
+    decision and no accepted step on a glass with rejections."""
+    pot, fp, x0, t, H = small_glass
+    x0 = x0 + np.array([0.3 * H[0, 0], 0.5 * H[1, 1]])
+    dg, K, P, n = 5e-3, 3, 4, 30
+    a = orc.parallel(pot, fp, x0, t, H, dg, K, P, n, eq_tol=1e-6)
+    b = orc.parallel(pot, fp, x0, t, H, dg, K, P, n, eq_tol=1e-6, wrap_ends=True)
+    assert a["status"] == 0 and b["status"] == 0
+    assert np.any(a["log_eq"] == 0)
+    assert np.array_equal(a["log_eq"], b["log_eq"]) and np.array_equal(a["log_i"], b["log_i"])
+    np.testing.assert_allclose(b["E"], a["E"], rtol=1e-12)
+    assert orc.max_rel_disp(a["x"], b["x"], a["H"]) < 1e-9
+
+
+def test_wrap_moves_atoms_by_lattice_vectors_into_the_cell(orc, syn):
+    """orc_wrap: fractional coordinates end in [0, 1) and every shift is an
+    integer combination of the cell's columns."""
+    H = np.array([[5.0, 1.7], [0.0, 4.0]])
+    x = (syn.uniform(31, 200).reshape(100, 2) - 0.5) * 30.0
+    w = orc.wrap(x, H)
+    s = np.linalg.solve(H, w.T).T
+    assert np.all(s >= -1e-12) and np.all(s < 1.0 + 1e-12)
+    m = np.linalg.solve(H, (x - w).T).T
+    np.testing.assert_allclose(m, np.round(m), atol=1e-9)
