@@ -211,9 +211,38 @@ def wrap(x, H):
     return x
 
 
-def parallel(pot, fp, x, types, H, dgamma, K, P, n_steps, eq_tol, n_threads=1, log_cap=100000,
-             K_max=0, wrap_ends=False):
+def triangularise(x, H):
+    x, H = _pos(x).copy(), _pos(H).copy()
+    lib().orc_triangularise(H.shape[0], x.shape[0], _p(x), _p(H))
+    return x, H
+
+
+def deform(x, H, F, Hlab=None):
+    """One increment of a deformation history; returns (x, H, Hlab)."""
+    x, H, F = _pos(x).copy(), _pos(H).copy(), _pos(F)
+    Hl = H.copy() if Hlab is None else _pos(Hlab).copy()
+    lib().orc_deform(H.shape[0], x.shape[0], _p(x), _p(H), _p(Hl), _p(F))
+    return x, H, Hl
+
+
+def aqs_history(pot, fp, x, types, H, F_steps, Hlab=None):
     x, t, H = _pos(x).copy(), _types(types), _pos(H).copy()
+    Hl = H.copy() if Hlab is None else _pos(Hlab).copy()
+    F = _pos(F_steps)
+    n_steps = F.shape[0]
+    E, tau, D = np.zeros(n_steps), np.zeros(n_steps), np.zeros(n_steps)
+    it = np.zeros(n_steps, dtype=np.int64)
+    st = lib().orc_aqs_history(C.byref(pot), C.byref(fp), x.shape[0], _p(x), _p(t, C.c_int32),
+                               _p(H), _p(Hl), C.c_double(0.0), _p(F), n_steps, _p(E), _p(tau),
+                               _p(it, C.c_int64), _p(D))
+    return dict(x=x, H=H, Hlab=Hl, status=st, E=E, tau=tau, iters=it, D=D)
+
+
+def parallel(pot, fp, x, types, H, dgamma, K, P, n_steps, eq_tol, n_threads=1, log_cap=100000,
+             K_max=0, wrap_ends=False, F_steps=None, Hlab=None):
+    x, t, H = _pos(x).copy(), _types(types), _pos(H).copy()
+    Hl = H.copy() if Hlab is None else _pos(Hlab).copy()
+    Fs = None if F_steps is None else _pos(F_steps)
     E, tau, D = np.zeros(n_steps), np.zeros(n_steps), np.zeros(n_steps)
     it = np.zeros(n_steps, dtype=np.int64)
     li = np.zeros(log_cap, dtype=np.int64)
@@ -226,9 +255,10 @@ def parallel(pot, fp, x, types, H, dgamma, K, P, n_steps, eq_tol, n_threads=1, l
                             C.c_double(dgamma), K, P, n_steps, C.c_double(eq_tol), n_threads,
                             _p(E), _p(tau), _p(it, C.c_int64), _p(D), _p(li, C.c_int64),
                             _p(lc, C.c_int32), _p(le, C.c_uint8), _p(lm), C.c_int64(log_cap),
-                            C.byref(stats), int(K_max), _p(Kp, C.c_int32), int(bool(wrap_ends)))
+                            C.byref(stats), int(K_max), _p(Kp, C.c_int32), int(bool(wrap_ends)),
+                            _p(Fs), _p(Hl) if Fs is not None else None)
     n = min(stats.n_log, log_cap)
-    return dict(x=x, H=H, status=st, E=E, tau=tau, iters=it, D=D,
+    return dict(x=x, H=H, Hlab=Hl, status=st, E=E, tau=tau, iters=it, D=D,
                 log_iter=li[:n], log_i=lc[:n], log_eq=le[:n], log_m=lm[:n],
                 iterations=stats.iterations, fire_iters_total=stats.fire_iters_total,
                 K_pass=Kp[:stats.iterations])

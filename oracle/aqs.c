@@ -24,15 +24,24 @@
 #include <string.h>
 #include "oracle.h"
 
-int orc_aqs(const orc_potential* pot, const orc_fire_params* fp, int n, double* x,
-            const int32_t* types, double* H, double dgamma, int n_steps, double* E_k,
-            double* tau_k, int64_t* iters_k, double* D_k) {
+/* the deformation increment of step k: simple shear by dgamma (Eq. 16), or
+ * the k-th matrix of a deformation history F (n_steps x d x d) */
+static void increment(int dim, int n, double* x, double* H, double* Hlab, double dgamma,
+                      const double* F, int k) {
+  if (F) orc_deform(dim, n, x, H, Hlab, F + (size_t)k * dim * dim);
+  else orc_affine_shear(dim, n, x, H, dgamma);
+}
+
+int orc_aqs_history(const orc_potential* pot, const orc_fire_params* fp, int n, double* x,
+                    const int32_t* types, double* H, double* Hlab, double dgamma, const double* F,
+                    int n_steps, double* E_k, double* tau_k, int64_t* iters_k, double* D_k) {
   int dim = pot->dim;
+  if (F && !Hlab) return ORC_ERR_INVALID_ARG;
   size_t nd = (size_t)n * dim;
   double* xa = malloc(nd * sizeof(double));
   int status = ORC_OK;
   for (int k = 0; k < n_steps; k++) {
-    orc_affine_shear(dim, n, x, H, dgamma); /* F_N^(dgamma) r_{k-1} */
+    increment(dim, n, x, H, Hlab, dgamma, F, k); /* F_N^(dgamma) r_{k-1} */
     memcpy(xa, x, nd * sizeof(double));
     int64_t it;
     double e, fm, tau;
@@ -46,6 +55,13 @@ int orc_aqs(const orc_potential* pot, const orc_fire_params* fp, int n, double* 
   }
   free(xa);
   return status;
+}
+
+int orc_aqs(const orc_potential* pot, const orc_fire_params* fp, int n, double* x,
+            const int32_t* types, double* H, double dgamma, int n_steps, double* E_k,
+            double* tau_k, int64_t* iters_k, double* D_k) {
+  return orc_aqs_history(pot, fp, n, x, types, H, NULL, dgamma, NULL, n_steps, E_k, tau_k,
+                         iters_k, D_k);
 }
 
 int64_t orc_alg1_decide(int P_eff, const int32_t* K_i, const uint8_t* eq, int32_t* first_fail) {
@@ -71,9 +87,11 @@ typedef struct {
   int n;
   const int32_t* types;
   double dgamma;
+  const double* F; /* the chain's fine increments (NULL: simple shear by dgamma) */
   int K_i;
   double* x;     /* in: level-I start; out: chain end */
   double* H;     /* in/out */
+  double* Hlab;  /* in/out, laboratory cell (histories only) */
   double* x_out; /* out: F(start), the outgoing configuration */
   double* E, *tau, *D;
   int64_t* iters;
@@ -92,8 +110,8 @@ static void* run_chain(void* arg) {
   c->iters_total += it;
   memcpy(c->x_out, c->x, nd * sizeof(double));
   if (c->status != ORC_OK) return NULL;
-  c->status = orc_aqs(c->pot, c->fp, c->n, c->x, c->types, c->H, c->dgamma, c->K_i, c->E,
-                      c->tau, c->iters, c->D);
+  c->status = orc_aqs_history(c->pot, c->fp, c->n, c->x, c->types, c->H, c->Hlab, c->dgamma,
+                              c->F, c->K_i, c->E, c->tau, c->iters, c->D);
   for (int k = 0; k < c->K_i; k++) c->iters_total += c->iters[k];
   return NULL;
 }
@@ -103,8 +121,9 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
                  double eq_tol, int n_threads, double* E_k, double* tau_k, int64_t* iters_k,
                  double* D_k, int64_t* log_iter, int32_t* log_i, uint8_t* log_eq, double* log_m,
                  int64_t log_cap, orc_parallel_stats* stats, int K_max, int32_t* K_pass,
-                 int wrap_ends) {
+                 int wrap_ends, const double* F_steps, double* Hlab) {
   if (K < 1 || P < 1 || n_steps < 0) return ORC_ERR_INVALID_ARG;
+  if (F_steps && !Hlab) return ORC_ERR_INVALID_ARG;
   const int Kcap = K_max > K ? K_max : K; /* longest chain any pass can have */
   const int adaptive = K_max > K;
   int dim = pot->dim;
@@ -113,6 +132,7 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
   double* xo = malloc(nd * sizeof(double) * P);   /* outgoing configurations */
   double* Hs = malloc(sizeof(double) * 9 * P);  /* chain cells, sheared along the chain */
   double* H1 = malloc(sizeof(double) * 9 * P);  /* level-I cells: chain i starts at i dgamma^c */
+  double* HL = malloc(sizeof(double) * 9 * P);  /* laboratory cells of the chains (histories) */
   double* cE = malloc(sizeof(double) * (size_t)Kcap * P);
   double* cT = malloc(sizeof(double) * (size_t)Kcap * P);
   double* cD = malloc(sizeof(double) * (size_t)Kcap * P);
@@ -131,15 +151,28 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
     if (P_eff > P) P_eff = P;
     for (int i = 0; i < P_eff; i++) Ki[i] = K;
     if (rem < (int64_t)P_eff * K) Ki[P_eff - 1] = (int32_t)(rem - (int64_t)(P_eff - 1) * K);
-    /* level I: r^c_iK = F_N^(i dgamma^c) r_star (Sec. 3.2, Eq. 18) */
+    /* level I: r^c_iK = F_N^(i dgamma^c) r_star (Sec. 3.2, Eq. 18).  With a
+     * deformation history the coarse map is the product of the i K fine
+     * increments that follow the current step, applied one after the other
+     * (the sequence chain i-1 applies along its way), so that chain i starts
+     * in exactly the cell in which chain i-1 ends. */
     for (int i = 0; i < P_eff; i++) {
       memcpy(xs + i * nd, x, nd * sizeof(double));
       memcpy(Hs + 9 * i, H, sizeof(double) * dim * dim);
-      orc_affine_shear(dim, n, xs + i * nd, Hs + 9 * i, i * dgc);
+      if (F_steps) {
+        memcpy(HL + 9 * i, Hlab, sizeof(double) * dim * dim);
+        for (int s = 0; s < i * K; s++)
+          orc_deform(dim, n, xs + i * nd, Hs + 9 * i, HL + 9 * i,
+                     F_steps + (size_t)(n_cur + s) * dim * dim);
+      } else {
+        orc_affine_shear(dim, n, xs + i * nd, Hs + 9 * i, i * dgc);
+      }
       memcpy(H1 + 9 * i, Hs + 9 * i, sizeof(double) * dim * dim);
       chain_job* c = &jobs[i];
       c->pot = pot; c->fp = fp; c->n = n; c->types = types; c->dgamma = dgamma;
       c->K_i = Ki[i]; c->x = xs + i * nd; c->H = Hs + 9 * i; c->x_out = xo + i * nd;
+      c->F = F_steps ? F_steps + (size_t)(n_cur + (int64_t)i * K) * dim * dim : NULL;
+      c->Hlab = F_steps ? HL + 9 * i : NULL;
       c->E = cE + (size_t)i * Kcap; c->tau = cT + (size_t)i * Kcap;
       c->D = cD + (size_t)i * Kcap; c->iters = cI + (size_t)i * Kcap;
     }
@@ -191,6 +224,7 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
     /* r_star <- r_q (end of chain `last`), H follows */
     memcpy(x, xs + (size_t)last * nd, nd * sizeof(double));
     memcpy(H, Hs + 9 * last, sizeof(double) * dim * dim);
+    if (F_steps) memcpy(Hlab, HL + 9 * last, sizeof(double) * dim * dim);
     n_cur += q;
     iter++;
     if (adaptive) {
@@ -205,7 +239,7 @@ int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, dou
     stats->fire_iters_total = fire_total;
     stats->n_log = n_log;
   }
-  free(xs); free(xo); free(Hs); free(H1); free(cE); free(cT); free(cD); free(cI);
+  free(xs); free(xo); free(Hs); free(H1); free(HL); free(cE); free(cT); free(cD); free(cI);
   free(jobs); free(th); free(Ki); free(eq);
   return status;
 }

@@ -84,6 +84,122 @@ void orc_affine_shear(int dim, int n, double* x, double* H, double dgamma) {
   orc_affine_map(dim, n, x, H, F);
 }
 
+void orc_triangularise(int dim, int n, double* x, double* H) {
+  /* Gram-Schmidt on the Bravais vectors (columns of H): q_0 along h_0, q_1 the
+   * part of h_1 orthogonal to q_0, q_2 = q_0 x q_1 (3D).  With Q = [q_0 q_1
+   * q_2], R = Q^T H is upper triangular with a positive diagonal (det H > 0),
+   * and x <- Q^T x rotates the configuration rigidly with the cell, which
+   * leaves every pair distance and the energy unchanged. */
+  double q[3][3] = {{0}}, h[3][3];
+  for (int c = 0; c < dim; c++)
+    for (int a = 0; a < dim; a++) h[c][a] = H[a * dim + c]; /* h[c] = column c */
+  double l0 = 0.0;
+  for (int a = 0; a < dim; a++) l0 += h[0][a] * h[0][a];
+  l0 = sqrt(l0);
+  for (int a = 0; a < dim; a++) q[0][a] = h[0][a] / l0;
+  double p = 0.0;
+  for (int a = 0; a < dim; a++) p += q[0][a] * h[1][a];
+  double l1 = 0.0;
+  for (int a = 0; a < dim; a++) {
+    q[1][a] = h[1][a] - p * q[0][a];
+    l1 += q[1][a] * q[1][a];
+  }
+  l1 = sqrt(l1);
+  for (int a = 0; a < dim; a++) q[1][a] /= l1;
+  if (dim == 3) {
+    q[2][0] = q[0][1] * q[1][2] - q[0][2] * q[1][1];
+    q[2][1] = q[0][2] * q[1][0] - q[0][0] * q[1][2];
+    q[2][2] = q[0][0] * q[1][1] - q[0][1] * q[1][0];
+  }
+  double R[9];
+  for (int a = 0; a < dim; a++)
+    for (int c = 0; c < dim; c++) {
+      double v = 0.0;
+      if (c >= a)
+        for (int k = 0; k < dim; k++) v += q[a][k] * h[c][k];
+      R[a * dim + c] = v;
+    }
+  for (int i = 0; i < n; i++) {
+    double y[3];
+    for (int a = 0; a < dim; a++) {
+      double v = 0.0;
+      for (int k = 0; k < dim; k++) v += q[a][k] * x[i * dim + k];
+      y[a] = v;
+    }
+    for (int a = 0; a < dim; a++) x[i * dim + a] = y[a];
+  }
+  memcpy(H, R, sizeof(double) * dim * dim);
+}
+
+/* rows q[a] of the orthonormal frame Q of Gram-Schmidt on the columns of a
+ * cell G (the frame in which G is upper triangular with a positive diagonal) */
+static void gs_frame(int dim, const double* G, double q[3][3]) {
+  double h[3][3];
+  for (int c = 0; c < dim; c++)
+    for (int a = 0; a < dim; a++) h[c][a] = G[a * dim + c];
+  double l0 = 0.0;
+  for (int a = 0; a < dim; a++) l0 += h[0][a] * h[0][a];
+  l0 = sqrt(l0);
+  for (int a = 0; a < dim; a++) q[0][a] = h[0][a] / l0;
+  double p = 0.0;
+  for (int a = 0; a < dim; a++) p += q[0][a] * h[1][a];
+  double l1 = 0.0;
+  for (int a = 0; a < dim; a++) {
+    q[1][a] = h[1][a] - p * q[0][a];
+    l1 += q[1][a] * q[1][a];
+  }
+  l1 = sqrt(l1);
+  for (int a = 0; a < dim; a++) q[1][a] /= l1;
+  if (dim == 3) {
+    q[2][0] = q[0][1] * q[1][2] - q[0][2] * q[1][1];
+    q[2][1] = q[0][2] * q[1][0] - q[0][0] * q[1][2];
+    q[2][2] = q[0][0] * q[1][1] - q[0][1] * q[1][0];
+  }
+}
+
+void orc_deform(int dim, int n, double* x, double* H, double* Hlab, const double* F) {
+  /* The history acts on the laboratory cell, Hlab <- F Hlab (Eq. 1).  The
+   * stored cell is its upper-triangular form R = Q^T Hlab (Q from
+   * Gram-Schmidt), so the stored configuration is the laboratory one seen in
+   * the frame Q.  One increment maps stored positions by
+   *   M = Q_new^T F Q_old        (r_lab <- F r_lab, Eq. 3, in the two frames)
+   * which is upper triangular, and sets H <- R_new.  For simple shear Q stays
+   * the identity and M = F exactly. */
+  double qo[3][3] = {{0}}, qn[3][3] = {{0}}, Hn[9], M[9], T[9];
+  gs_frame(dim, Hlab, qo);
+  for (int a = 0; a < dim; a++)
+    for (int c = 0; c < dim; c++) {
+      double v = 0.0;
+      for (int k = 0; k < dim; k++) v += F[a * dim + k] * Hlab[k * dim + c];
+      Hn[a * dim + c] = v;
+    }
+  memcpy(Hlab, Hn, sizeof(double) * dim * dim);
+  gs_frame(dim, Hlab, qn);
+  /* T = F Q_old (columns of Q_old are the rows qo[.]), M = Q_new^T T */
+  for (int a = 0; a < dim; a++)
+    for (int c = 0; c < dim; c++) {
+      double v = 0.0;
+      for (int k = 0; k < dim; k++) v += F[a * dim + k] * qo[c][k];
+      T[a * dim + c] = v;
+    }
+  for (int a = 0; a < dim; a++)
+    for (int c = 0; c < dim; c++) {
+      double v = 0.0;
+      for (int k = 0; k < dim; k++) v += qn[a][k] * T[k * dim + c];
+      M[a * dim + c] = c < a ? 0.0 : v;
+    }
+  double Hdummy[9];
+  memcpy(Hdummy, H, sizeof(double) * dim * dim);
+  orc_affine_map(dim, n, x, Hdummy, M);
+  for (int a = 0; a < dim; a++)
+    for (int c = 0; c < dim; c++) {
+      double v = 0.0;
+      if (c >= a)
+        for (int k = 0; k < dim; k++) v += qn[a][k] * Hlab[k * dim + c];
+      H[a * dim + c] = v;
+    }
+}
+
 void orc_wrap(int dim, int n, double* x, const double* H) {
   /* fractional coordinates s = H^-1 r by back substitution (H upper
    * triangular), then r <- r - H floor(s) */

@@ -70,6 +70,18 @@ double orc_half_min_width(int dim, const double* H);
 /* simple-shear affine map F^(dgamma) (Eq. 16): r_i <- F r_i for all atoms
  * (Eq. 3) and H <- F H (Eq. 1) */
 void orc_affine_shear(int dim, int n, double* x, double* H, double dgamma);
+/* rotates the cell and the configuration rigidly to the frame in which H is
+ * upper triangular with a positive diagonal (H = Q R, H <- R, r <- Q^T r);
+ * requires det H > 0 */
+void orc_triangularise(int dim, int n, double* x, double* H);
+/* one deformation increment with a general d x d matrix F (row-major) that
+ * acts on the laboratory cell Hlab (in/out, general): Hlab <- F Hlab (Eq. 1).
+ * The stored cell H (in/out) is the upper-triangular form of Hlab (Gram-
+ * Schmidt frame Q, H = Q^T Hlab) and stored positions follow by
+ * M = Q_new^T F Q_old (Eq. 3 in the two frames).  Simple shear (Eq. 16) with
+ * Hlab = H gives exactly orc_affine_shear; the paper's pull-push ("pure")
+ * shear matrix [[1, dg_x], [dg_y, 1]] (Sec. 2.2) rotates the frame. */
+void orc_deform(int dim, int n, double* x, double* H, double* Hlab, const double* F);
 /* maps every atom into the cell, r <- r - H floor(H^-1 r) (by whole lattice
  * vectors; the configuration is unchanged under periodic boundaries) */
 void orc_wrap(int dim, int n, double* x, const double* H);
@@ -112,6 +124,14 @@ double orc_max_rel_disp(int dim, int n, const double* a, const double* b, const 
 int orc_aqs(const orc_potential* pot, const orc_fire_params* fp, int n, double* x,
             const int32_t* types, double* H, double dgamma, int n_steps, double* E_k,
             double* tau_k, int64_t* iters_k, double* D_k);
+/* the same protocol under a deformation history: step k applies the k-th
+ * d x d matrix of F (n_steps x d x d, row-major) to the laboratory cell Hlab
+ * (in/out; must be given with F) by orc_deform instead of the simple shear
+ * by dgamma (F = NULL gives orc_aqs).  Covers pure (pull-push) shear
+ * (Sec. 2.2) and cyclic protocols (Sec. 5). */
+int orc_aqs_history(const orc_potential* pot, const orc_fire_params* fp, int n, double* x,
+                    const int32_t* types, double* H, double* Hlab, double dgamma, const double* F,
+                    int n_steps, double* E_k, double* tau_k, int64_t* iters_k, double* D_k);
 
 /* ---- two-level parallel stepping (Sec. 3, Algorithm 1) ---- */
 typedef struct {
@@ -136,13 +156,18 @@ typedef struct {
  * wrap_ends = 1 maps every chain's end into its cell (orc_wrap) before the
  * equality tests.  Positions are only defined up to lattice vectors, so the
  * decisions and the trajectory must not change; the tests use it to check
- * that the tests are made at the shared strain's cell. */
+ * that the tests are made at the shared strain's cell.
+ * F_steps (nullable, n_steps x d x d): a deformation history as in
+ * orc_aqs_history, with the laboratory cell Hlab in/out; level I then applies
+ * the fine increments one after the other (for simple shear F^(a) F^(b) = F^(a+b), so this is the paper's
+ * coarse map; for other histories it is the reading that keeps chain i's
+ * start in the cell where chain i-1 ends). */
 int orc_parallel(const orc_potential* pot, const orc_fire_params* fp, int n, double* x,
                  const int32_t* types, double* H, double dgamma, int K, int P, int n_steps,
                  double eq_tol, int n_threads, double* E_k, double* tau_k, int64_t* iters_k,
                  double* D_k, int64_t* log_iter, int32_t* log_i, uint8_t* log_eq, double* log_m,
                  int64_t log_cap, orc_parallel_stats* stats, int K_max, int32_t* K_pass,
-                 int wrap_ends);
+                 int wrap_ends, const double* F_steps, double* Hlab);
 
 /* Pure decision rule of Algorithm 1 (lines after the level-II loop): given
  * the chain lengths K_i (i = 0..P_eff-1) and the equality outcomes eq[i] for
