@@ -17,11 +17,20 @@ Reported (one JSON line on rank 0):
            host -> device positions, the pass, device -> host positions and
            per-step observables, all inside the timed region
   roofline the persistent minimiser kernel (FP32 pipe; its FP64 work noted)
-  cpu_baseline  the FP64 oracle on a bounded sample of this workload
+  cpu_baseline  the FP64 oracle on the host cores: complete converged AQS
+           steps of the N = 256 glass (the small configuration of this
+           workload; the all-pairs oracle cannot finish an N = 4096 step in
+           the time a benchmark run allows)
+  fp64_sequential_gpu_baseline  plain sequential AQS with the same kernels in
+           FP64 mode, one replica, no batching: 20 steps sampled at four
+           points of the timed strain window
   clocks   SM clocks and throttle reasons sampled during the timed region
 
 ``--impl reference`` times the oracle instead (the CPU program this project is
-checked against) on the same workload and prints the same kind of line.
+checked against): each step is one converged AQS step of the N = 256 glass.
+``--workload oracle-threads`` reproduces the paper's own kind of measurement
+with the oracle on host threads (sequential AQS against Algorithm 1 with one
+chain per thread).
 """
 from __future__ import annotations
 
@@ -29,6 +38,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import subprocess
 import tempfile
 import sys
@@ -42,18 +52,20 @@ sys.path.insert(0, ROOT)
 N_ATOMS, P_CHAINS, K_FINE, DGAMMA, GAMMA_END = 4096, 16, 10, 1e-4, 0.2
 METRIC = "converged AQS strain steps/s (two-level parallel stepping, |F|max<1e-10)"
 UNIT = "steps/s"
-# FP32 peak of GB300 from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop
-# (FMA) x 2.07 GHz maximum SM clock
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# algorithmic FP32 flops of one relative pair-force visit (both atoms inside
-# the cutoff; FMA counted as 2, reciprocal square root as 1) and FP64 flops of
-# one FP64 pair visit -- counted from minimize.cu
-FLOP32_PER_PAIR = 62
+# Algorithmic flops of the method per list entry (one atom looking at one
+# neighbour) of a 2D shifted-force LJ force-and-energy evaluation, FMA = 2:
+#   separation d = (q_j - q_i) + image offset   4
+#   r^2, cutoff test                            4
+#   u = 1/r^2, u^3, u^4, u^7, r^-1              6
+#   phi = A u^7 + B u^4 + C r^-1                5
+#   F_i += phi d                                4
+#   U_sf = e12 u^6 - e6 u^3 - Uc - (r - rc) dUc 7
+# = 30.  (The kernel's own mixed-precision formulation, F_ref + dF by exact
+# divided differences, executes about 62 FP32 flops per visit; that count is
+# reported beside it as "kernel_flop_per_visit".)
+FLOP32_PER_PAIR = 30
+KERNEL_FLOP32_PER_VISIT = 62
 FLOP64_PER_PAIR = 32
-# mean FIRE iterations per accepted fine step of this workload, used only to
-# express the reference arm's oracle sample in steps/s (measured by this
-# benchmark's own arm on the seed-0 glass)
-ITERS_PER_STEP_REF = 23000
 # DRAM bytes (read + write) of the dominant kernel from one ncu capture each
 # (--set full, clocks unlocked), for the roofline's "traffic"; a capture is
 # valid only for the kernel version it was taken on.
@@ -135,6 +147,38 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def fp32_peak_tflops():
+    """FP32 peak of the device from its unit counts: SMs (queried) x 128 FP32
+    lanes x 2 flop (FMA) x the maximum SM clock (measured peaks file, else
+    nvidia-smi, else 2.07 GHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = _peaks().get("sm_max_mhz")
+    if not mhz:
+        try:
+            out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm",
+                                  "--format=csv,noheader,nounits", "-i", "0"],
+                                 capture_output=True, text=True, timeout=20).stdout
+            mhz = float(out.split()[0])
+        except Exception:
+            mhz = 2070.0
+    return sms * 128 * 2 * float(mhz) * 1e6 / 1e12, sms, float(mhz)
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def host_desc():
+    return {"nproc": os.cpu_count(), "cpu": cpu_model(), "machine": platform.machine()}
+
+
 def combine_ranks(secs, units, device):
     """Whole-job figures over the ranks (weak scaling, one glass per rank):
     the sum of the units every rank processed and the slowest rank's time.
@@ -150,21 +194,33 @@ def combine_ranks(secs, units, device):
     return float(tt[1]), float(mx[0])
 
 
-def oracle_iteration_rate(n_iters: int, seed: int = 0):
-    """FIRE iterations per second of the FP64 oracle on this workload's size
-    (all-pairs forces dominate, so the rate does not depend on the
-    configuration; the seeded start of the workload is used)."""
+def oracle_steps(n_steps=None, budget_s=None, dgamma=DGAMMA):
+    """Complete converged AQS steps (Eq. 12: affine dgamma, then FIRE to
+    |F|max < 1e-10) of the FP64 all-pairs oracle on one host core, from the
+    stored N = 256 glass (the small configuration of this workload).  Runs
+    n_steps steps, or steps one at a time until budget_s seconds are used (at
+    least two).  Returns (steps, seconds, FIRE iterations)."""
     import oracle
     from paper_2507_20802_gb300 import synthetic as syn
     oracle.build()
-    x, t, H = syn.random_glass_start(N_ATOMS, 2, seed)
+    g = np.load(os.path.join(ROOT, "tests", "golden", "glass_2d_n256_s0.npz"))
+    x, t, H = g["x"], g["types"], g["H"]
     pot = oracle.make_potential(2, syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR)
-    fp = oracle.make_fire(**dict(syn.FIRE, max_iter=n_iters, tol=1e-300))
-    t0 = time.perf_counter()
-    r = oracle.fire(pot, fp, x, t, H)
-    dt = time.perf_counter() - t0
-    evals = r["iters"] + 1
-    return evals / dt, evals, dt
+    fp = oracle.make_fire(**syn.FIRE)
+    steps, secs, iters = 0, 0.0, 0
+    while True:
+        t0 = time.perf_counter()
+        r = oracle.aqs(pot, fp, x, t, H, dgamma, 1)
+        secs += time.perf_counter() - t0
+        assert r["status"] == 0
+        x, H = r["x"], r["H"]
+        steps += 1
+        iters += int(r["iters"][0])
+        if n_steps is not None and steps >= n_steps:
+            break
+        if budget_s is not None and secs >= budget_s and steps >= 2:
+            break
+    return steps, secs, iters
 
 
 def run_reference(args):
@@ -172,26 +228,72 @@ def run_reference(args):
     if rank != 0:
         return 0
     per_step = []
-    n_it = 12
     for i in range(args.warmup + args.steps):
-        rate, evals, dt = oracle_iteration_rate(n_it)
+        n, dt, it = oracle_steps(n_steps=1)
         if i >= args.warmup:
-            per_step.append((evals, dt))
-    evals = sum(e for e, _ in per_step)
-    secs = sum(d for _, d in per_step)
-    value = (evals / secs) / ITERS_PER_STEP_REF
+            per_step.append((dt, it))
+    secs = sum(d for d, _ in per_step)
+    value = len(per_step) / secs
+    sample = ("each step: one complete AQS step (dgamma=1e-4, FIRE to |F|max<1e-10, %d FIRE "
+              "iterations on average) of the FP64 all-pairs oracle on the N=256 glass, one host "
+              "core; the N=4096 glass of this workload costs (4096/256)^2 = 256x more per "
+              "iteration in this O(N^2) oracle and ~10x more iterations per step"
+              % round(np.mean([i for _, i in per_step])))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / max(1, len(per_step)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": CONFIG,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n_it} FIRE iterations of the FP64 all-pairs oracle "
-                                       f"at N={N_ATOMS} per step, converted with "
-                                       f"{ITERS_PER_STEP_REF} FIRE iterations per accepted "
-                                       f"fine step"},
+                             "sample": sample, "host": host_desc()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_oracle_threads(args):
+    """The paper's own kind of measurement (Sec. 4) with the FP64 oracle on
+    this machine's host cores: sequential AQS (Eq. 12) against Algorithm 1
+    with one level-II chain per POSIX thread, on the stored N = 256 glass,
+    dgamma = 1e-4.  Prints one line with a row per (P, K): wall seconds,
+    speed-up over sequential, passes, rejections, and whether the energies
+    equal the sequential run's."""
+    import oracle
+    from paper_2507_20802_gb300 import synthetic as syn
+    oracle.build()
+    g = np.load(os.path.join(ROOT, "tests", "golden", "glass_2d_n256_s0.npz"))
+    pot = oracle.make_potential(2, syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR)
+    fp = oracle.make_fire(**syn.FIRE)
+    n = args.oracle_steps
+    t0 = time.perf_counter()
+    seq = oracle.aqs(pot, fp, g["x"], g["types"], g["H"], DGAMMA, n)
+    t_seq = time.perf_counter() - t0
+    assert seq["status"] == 0
+    rows = []
+    for K in args.oracle_K:
+        for P in args.oracle_P:
+            if P > (os.cpu_count() or 1):
+                continue
+            t0 = time.perf_counter()
+            r = oracle.parallel(pot, fp, g["x"], g["types"], g["H"], DGAMMA, K, P, n,
+                                eq_tol=1e-6, n_threads=P)
+            dt = time.perf_counter() - t0
+            assert r["status"] == 0
+            rows.append({"P": P, "K": K, "threads": P, "wall_s": dt, "speedup": t_seq / dt,
+                         "passes": int(r["iterations"]),
+                         "rejections": int(np.sum(r["log_eq"] == 0)),
+                         "energies_equal_sequential": bool(np.allclose(r["E"], seq["E"],
+                                                                       rtol=1e-9))})
+    best = max((r["speedup"] for r in rows), default=1.0)
+    line = {"metric": "Algorithm 1 speed-up over sequential AQS, FP64 oracle on host threads",
+            "value": best, "unit": "x", "n_gpus": 0, "steps": n, "warmup": 0,
+            "ms_per_step": 1e3 * t_seq / n, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "N=256 2D binary LJ glass (seed 0), dgamma=1e-4, %d steps, "
+                                   "FP64 all-pairs oracle, one chain per POSIX thread" % n},
+            "host": host_desc(), "sequential_s": t_seq, "rows": rows,
+            "paper": "2.02-6.33x average speed-up at 4-32 threads (CPU, hardware not stated)"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -378,6 +480,7 @@ def run_batch64(args):
     value = 64 * args.steps / secs
     kern_s = st["kernel_ms"] / 1e3
     achieved = st["pairs32"] * FLOP32_PER_PAIR / kern_s / 1e12 if kern_s else 0.0
+    peak32, n_sm, mhz = fp32_peak_tflops()
     config = {"workload": "64 independent 2D binary LJ glasses, N log-uniform in [1024, 16384] "
                           "(sum %d), plain AQS dgamma=5e-5, batched mixed precision" % int(sizes.sum()),
               "n_glasses": 64, "atoms_total": int(sizes.sum()), "dgamma": 5e-5,
@@ -385,8 +488,11 @@ def run_batch64(args):
     _line("converged AQS glass-steps/s (64 glasses batched)", value, "glass-steps/s", args,
           1e3 * secs / max(1, args.steps), config,
           {"gpu_launches": A.aqs_launch_count() - l0, "clocks": clk.summary(),
-           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                        "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32,
+                        "unit": "TFLOP/s", "frac": achieved / peak32, "traffic": None,
+                        "flop_per_list_entry": FLOP32_PER_PAIR,
+                        "peak_note": "FP32 peak derived: %d SMs x 128 lanes x 2 x %.0f MHz"
+                                     % (n_sm, mhz)},
            "detail": {"fire_iters_per_step_mean": float(out["iters"].mean()),
                       "fire_iters_per_step_max": int(out["iters"].max()), "quench_iters_max": quench,
                       "slowest_glass": {"index": int(np.argmax(out["iters"].sum(axis=0))),
@@ -473,11 +579,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-iters", type=int, default=40)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0,
+                    help="host-core budget of the oracle CPU baseline (whole steps)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
-    ap.add_argument("--baseline-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d", "warm"], default="cfg1")
+    ap.add_argument("--baseline-steps", type=int, default=20)
+    ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d", "warm", "oracle-threads"],
+                    default="cfg1")
+    ap.add_argument("--oracle-steps", type=int, default=60)
+    ap.add_argument("--oracle-P", type=int, nargs="+", default=[4, 8, 16])
+    ap.add_argument("--oracle-K", type=int, nargs="+", default=[1, 10])
     ap.add_argument("--k-max", type=int, default=0,
                     help="> K: dynamic K up to this chain length (default: fixed K = 10)")
     ap.add_argument("--seeds", type=int, default=0,
@@ -500,6 +611,8 @@ def main():
         return run_warm(args) or 0
     if args.workload == "glass3d":
         return run_glass3d(args) or 0
+    if args.workload == "oracle-threads":
+        return run_oracle_threads(args) or 0
 
     import torch
     ws, rank, local = _dist()
@@ -561,9 +674,16 @@ def main():
     gpu_index = int((os.environ.get("CUDA_VISIBLE_DEVICES") or str(local)).split(",")[0]) \
         if (os.environ.get("CUDA_VISIBLE_DEVICES") or "").split(",")[0].isdigit() else local
     accepted, dev_ms, wall, iters, rej, stopped = 0, 0.0, 0.0, [], 0, 0
+    # r_star at four evenly spaced passes of the timed window: the FP64
+    # sequential baseline starts from these states (read back between passes,
+    # outside the device-timed region)
+    snap_at = sorted({int(k * args.steps / 4) for k in range(4)})
+    snaps = []
     barrier()
     with Clocks(gpu_index) as clk:
-        for _ in range(args.steps):
+        for ip in range(args.steps):
+            if rank == 0 and not args.no_baseline and ip in snap_at:
+                snaps.append((s.positions(), s.box()))
             flush.fill_(1.0)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -611,8 +731,11 @@ def main():
     flop32 = st["pairs32"] * FLOP32_PER_PAIR
     flop64 = st["pairs64"] * FLOP64_PER_PAIR
     achieved = flop32 / kern_s / 1e12 if kern_s > 0 else 0.0
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+    peak32, n_sm, mhz = fp32_peak_tflops()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak32,
+                "unit": "TFLOP/s", "frac": achieved / peak32,
+                "flop_per_list_entry": FLOP32_PER_PAIR,
+                "kernel_flop_per_visit": KERNEL_FLOP32_PER_VISIT,
                 "traffic": TRAFFIC_CFG1_PER_LAUNCH,
                 "traffic_note": "bytes per launch, ncu capture of one level-II chain launch",
                 "kernel": "k_minimize<2,mixed>",
@@ -620,49 +743,63 @@ def main():
                 "fp64_tflops": flop64 / kern_s / 1e12 if kern_s > 0 else 0.0,
                 "launches": st["launches"], "avg_launch_ms": st["kernel_ms"] / max(1, st["launches"]),
                 "pair_visits_fp32": st["pairs32"], "pair_visits_fp64": st["pairs64"],
-                "peak_note": "FP32 peak derived from 152 SMs x 128 lanes x 2 x 2.07 GHz"}
+                "peak_note": "FP32 peak derived: %d SMs (queried) x 128 lanes x 2 x %.0f MHz"
+                             % (n_sm, mhz)}
 
     # ---------------- plain FP64 sequential GPU AQS on the same glass (the
     # denominator of the speed-up target): same kernels in FP64 mode, one
-    # replica, no batching, no warm start, a bounded number of steps
+    # replica, no batching, no warm start; baseline_steps steps split over the
+    # four r_star states taken across the timed window
     base = None
-    if rank == 0 and not args.no_baseline:
-        xb_ = s.positions()
-        b = A.System(xb_, t, s.box()[None], [N_ATOMS], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
-                     precision=A.AQS_FP64)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        ob = b.run_sequential(DGAMMA, args.baseline_steps)
-        e1.record()
-        e1.synchronize()
-        bsec = e0.elapsed_time(e1) / 1e3
-        # a 2-step sample is dominated by whether those steps hold an event,
-        # so the baseline is also stated for the steps of the timed region:
-        # its FIRE iterations per accepted step at the FP64 time per iteration
-        t_it64 = bsec / max(1, int(ob["iters"].sum()))
+    if rank == 0 and not args.no_baseline and snaps:
+        per = max(1, -(-args.baseline_steps // len(snaps)))
+        bsec, bsteps, bits, csize = 0.0, 0, 0, 0
+        for xs_, Hs_ in snaps:
+            b = A.System(xs_, t, Hs_[None], [N_ATOMS], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
+                         precision=A.AQS_FP64)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ob = b.run_sequential(DGAMMA, per)
+            e1.record()
+            e1.synchronize()
+            bsec += e0.elapsed_time(e1) / 1e3
+            bsteps += per
+            bits += int(ob["iters"].sum())
+            csize = b.cluster_size()
+            b.close()
+        # the same comparison at equal work: the FP64 time per iteration times
+        # the FIRE iterations per accepted step of the timed region
+        t_it64 = bsec / max(1, bits)
         mean_acc = float(np.mean(iters)) if iters else float("nan")
         same = 1.0 / (mean_acc * t_it64)
-        base = {"value": args.baseline_steps / bsec, "unit": UNIT, "steps": args.baseline_steps,
-                "fire_iters_per_step": float(ob["iters"].mean()),
+        bval = bsteps / bsec
+        base = {"value": bval, "unit": UNIT, "steps": bsteps,
+                "sample": "%d steps from each of %d r_star states taken at timed passes %s"
+                          % (per, len(snaps), snap_at),
+                "fire_iters_per_step": bits / bsteps,
                 "us_per_fp64_iteration": 1e6 * t_it64,
                 "same_steps_value": same,
                 "same_steps_note": "FP64 time per iteration x FIRE iterations per accepted step "
                                    "of the timed region",
-                "cluster_size": b.cluster_size(),
-                "speedup_of_value": value / (args.baseline_steps / bsec),
+                "cluster_size": csize,
+                "occupancy_note": "one replica of %d atoms fills one cluster of %d CTAs, i.e. "
+                                  "%d of %d SMs: sequential AQS cannot use the rest"
+                                  % (N_ATOMS, csize, csize, n_sm),
+                "speedup_of_value": value / bval,
                 "speedup_same_steps": value / same}
-        b.close()
 
     # ---------------- CPU baseline (oracle, rank 0, N = 1 only)
     cpu = None
     mean_iters = float(np.mean(iters)) if iters else float("nan")
     if rank == 0 and ws == 1 and not args.no_cpu:
-        rate, evals, dt = oracle_iteration_rate(args.cpu_iters)
-        cpu = {"value": rate / mean_iters, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{evals} FIRE iterations of the FP64 all-pairs oracle at N={N_ATOMS} "
-                         f"({dt:.1f} s), divided by the {mean_iters:.0f} FIRE iterations per "
-                         f"accepted fine step measured in this run"}
+        nst, dt, oit = oracle_steps(budget_s=args.cpu_seconds)
+        cpu = {"value": nst / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d complete AQS steps (dgamma=1e-4, FIRE to |F|max<1e-10, %d FIRE "
+                         "iterations per step) of the FP64 all-pairs oracle on the N=256 glass "
+                         "in %.1f s on one host core; an N=4096 step of this workload costs "
+                         "about 256x more per iteration in the O(N^2) oracle" % (nst, oit / nst, dt),
+               "host": host_desc()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,

@@ -133,7 +133,8 @@ typedef struct {
 } aqs_min_result;
 
 /* Creates a system; copies pos/types.  Fails with AQS_ERR_BOX_TOO_SMALL when
- * the cell is too small for the cutoff and skin. */
+ * the cell is too small for the cutoff and skin, and with AQS_ERR_NONFINITE
+ * when a position is NaN or infinite. */
 aqs_status aqs_create_system(const aqs_system_desc* desc, aqs_system** out);
 void aqs_destroy_system(aqs_system* sys);
 
@@ -229,7 +230,8 @@ int aqs_num_replicas(const aqs_system* sys);
 int64_t aqs_num_atoms(const aqs_system* sys, int replica);
 /* out: host or device [n * dim], user order */
 aqs_status aqs_get_positions(const aqs_system* sys, int replica, double* out);
-/* pos: host or device [n * dim], user order; resets FIRE state of the replica */
+/* pos: host or device [n * dim], user order; resets FIRE state of the replica;
+ * AQS_ERR_NONFINITE (nothing written) if a coordinate is NaN or infinite */
 aqs_status aqs_set_positions(aqs_system* sys, int replica, const double* pos);
 aqs_status aqs_get_box(const aqs_system* sys, int replica, double* H);
 aqs_status aqs_set_box(aqs_system* sys, int replica, const double* H);
@@ -308,15 +310,18 @@ aqs_status aqs_run_sequential_warm(aqs_system* sys, const aqs_fire_params* fire,
  *   n         atoms, 2 <= n <= AQS_NOALLOC_MAX_ATOMS, else AQS_ERR_INVALID_ARG
  *   pos       device [n * dim], Cartesian
  *   types     device [n], values < pot->n_types
- *   box       host [dim * dim], upper-triangular cell (tilt in H[0][1] only);
+ *   box       host [dim * dim], upper-triangular cell with its tilt in H[0][1]
+ *             only (any other off-diagonal entry: AQS_ERR_INVALID_ARG);
  *             AQS_ERR_BOX_TOO_SMALL if 2 * max cutoff >= a perpendicular width
  *   pot       host, the potential as in aqs_potential
  *   forces    device [n * dim], written (force on each atom)
  *   energy_tau device [2], written: total energy, shear stress (1/V) dU/dgamma
  *   stream    cudaStream_t (NULL = legacy default stream); the call only
  *             enqueues work and returns without synchronising.
- * The first call on a device looks up the scratch array's device address with
- * cudaGetSymbolAddress while that device is current; make that first call
+ * Every call looks up the scratch array's device address with
+ * cudaGetSymbolAddress in the caller's current context (the address belongs
+ * to the context, so it is not cached).  The first call on a device also makes
+ * the runtime load the library's device code there; make that first call
  * before capturing a stream.  Every call shares the one scratch array and each
  * call overwrites every slot it later reads, so nothing has to be cleared, but
  * calls that overlap on the GPU (different streams, no ordering) race on it. */

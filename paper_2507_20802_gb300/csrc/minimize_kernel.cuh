@@ -160,10 +160,11 @@ struct Ctl {
 
 // Compensated ("float-float") sum on the FP32 pipe: TwoSum of Knuth (TAOCP
 // vol. 2, 4.2.2) followed by renormalisation (Dekker 1971).  The pair
-// (hi, lo) carries about 44 significant bits, so cross-thread sums of the FIRE
-// reductions keep FP64-level accuracy without FP64 instructions, whose issue
-// cost on GB300 (about 64 cycles per warp instruction per SM sub-partition)
-// would dominate an iteration.
+// (hi, lo) carries about 44 significant bits, so the cross-thread sums of
+// |F|^2 and |v|^2 (the FIRE mixing norms) keep near-FP64 accuracy without FP64
+// instructions, whose issue cost on GB300 (one warp instruction per ~32 cycles
+// per SM sub-partition) would dominate an iteration if every sum used them.
+// The FIRE power P = F.v, whose sign decides every step, is summed in FP64.
 struct FF {
   float hi, lo;
 };
@@ -179,6 +180,14 @@ __device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
   return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 __device__ __forceinline__ float nmaxf(float a, float b) { return (a != a || a > b) ? a : b; }
+// an FP64 value in two consecutive FP32 slots of a reduction record
+__device__ __forceinline__ void put_d(float* q, double d) {
+  q[0] = __int_as_float(__double2loint(d));
+  q[1] = __int_as_float(__double2hiint(d));
+}
+__device__ __forceinline__ double get_d(const float* q) {
+  return __hiloint2double(__float_as_int(q[1]), __float_as_int(q[0]));
+}
 
 // While the largest FP64 force exceeds this, mixed mode keeps evaluating in
 // FP64 (random starts and collisions), where FP32 would overflow.
@@ -671,7 +680,8 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
     double r[kNumRed];
 #pragma unroll
     for (int m = 0; m < kNumRed; m++) r[m] = 0.0;
-    float rf[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // DEV: fmax^2, P, |F|^2, |v|^2, max|delta|^2
+    float rf[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // DEV: fmax^2, -, |F|^2, |v|^2, max|delta|^2
+    double rp = 0.0;  // DEV: the FIRE power P = F.v, summed in FP64
 #pragma unroll
     for (int k = 0; k < APT; k++) {
       if constexpr (!LEAN) {
@@ -753,29 +763,31 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
         } else {
           pair_loop([&](int tj) { return coef32(coef[ti * A.nt + tj]); });
         }
-        float f2 = 0.f, pv = 0.f, v2 = 0.f, dd = 0.f;
+        float f2 = 0.f, v2 = 0.f, dd = 0.f;
+        double pv = 0.0;  // FP32 products are exact in FP64
 #pragma unroll
         for (int c = 0; c < D; c++) {
           const float fu = FR(k, c) + f[c];
           const float vk = V(k, c);
           FU(k, c) = fu;
           f2 = fmaf(fu, fu, f2);
-          pv = fmaf(fu, vk, pv);
+          pv = fma((double)fu, (double)vk, pv);
           v2 = fmaf(vk, vk, v2);
           dd = fmaf(di[c], di[c], dd);  // the published displacement
         }
         rf[0] = nmaxf(rf[0], f2);
-        rf[1] += pv;
+        rp += pv;
         rf[2] += f2;
         rf[3] += v2;
         rf[4] = nmaxf(rf[4], dd);
       }
     }
 
-    // ================= reduction (fixed order; FP64 or float-float) =================
+    // ================= reduction (fixed order; FP64, or float-float norms and FP64 power) =================
     const bool fast = MIXED && mode == kModeDev;  // uniform in the cluster
     double T[kNumRed];  // FP64 totals (valid in warp 0)
     float Tf[5];        // DEV totals (valid in warp 0)
+    double Pd = 0.0;    // DEV: the FIRE power, FP64 (valid in warp 0)
     if (!fast) {
 #pragma unroll
       for (int m = 0; m < kNumRed; m++) {
@@ -815,36 +827,39 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
       }
     } else {
       float m0 = rf[0], m4 = rf[4];
-      FF sp{rf[1], 0.f}, sf{rf[2], 0.f}, sv{rf[3], 0.f};
+      double sp = rp;
+      FF sf{rf[2], 0.f}, sv{rf[3], 0.f};
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         m0 = nmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
         m4 = nmaxf(m4, __shfl_xor_sync(0xffffffffu, m4, o));
-        sp = ff_add(sp, ff_shfl_xor(sp, o));
+        sp += __shfl_xor_sync(0xffffffffu, sp, o);
         sf = ff_add(sf, ff_shfl_xor(sf, o));
         sv = ff_add(sv, ff_shfl_xor(sv, o));
       }
       float* w32 = reinterpret_cast<float*>(wred);
       if (lane == 0) {
         float* q = w32 + warp * 8;
-        q[0] = m0; q[1] = m4; q[2] = sp.hi; q[3] = sp.lo;
+        q[0] = m0; q[1] = m4; put_d(q + 2, sp);
         q[4] = sf.hi; q[5] = sf.lo; q[6] = sv.hi; q[7] = sv.lo;
       }
       __syncthreads();
-      // butterfly over 8-float records (max, max, three float-float sums)
+      // butterfly over 8-float records (max, max, the FP64 power, two
+      // float-float sums)
       auto reduce8 = [&](const float* q, bool valid, float* out) {
         float a0 = valid ? q[0] : 0.f, a4 = valid ? q[1] : 0.f;
-        FF bp{valid ? q[2] : 0.f, valid ? q[3] : 0.f}, bf{valid ? q[4] : 0.f, valid ? q[5] : 0.f};
+        double bp = valid ? get_d(q + 2) : 0.0;
+        FF bf{valid ? q[4] : 0.f, valid ? q[5] : 0.f};
         FF bv{valid ? q[6] : 0.f, valid ? q[7] : 0.f};
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           a0 = nmaxf(a0, __shfl_xor_sync(0xffffffffu, a0, o));
           a4 = nmaxf(a4, __shfl_xor_sync(0xffffffffu, a4, o));
-          bp = ff_add(bp, ff_shfl_xor(bp, o));
+          bp += __shfl_xor_sync(0xffffffffu, bp, o);
           bf = ff_add(bf, ff_shfl_xor(bf, o));
           bv = ff_add(bv, ff_shfl_xor(bv, o));
         }
-        out[0] = a0; out[1] = a4; out[2] = bp.hi; out[3] = bp.lo;
+        out[0] = a0; out[1] = a4; put_d(out + 2, bp);
         out[4] = bf.hi; out[5] = bf.lo; out[6] = bv.hi; out[7] = bv.lo;
       };
       float* red32 = reinterpret_cast<float*>(red);
@@ -861,7 +876,8 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
         reduce8(rq, lane < C, o8);
         Tf[0] = o8[0];
         Tf[4] = o8[1];
-        Tf[1] = o8[2] + o8[3];
+        Pd = get_d(o8 + 2);
+        Tf[1] = (float)Pd;
         Tf[2] = o8[4] + o8[5];
         Tf[3] = o8[6] + o8[7];
       }
@@ -893,7 +909,7 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
           evals32++;
           acc32++;
           fm = sqrtf(Tf[0]);
-          finite = (Tf[0] < INFINITY) && (Tf[2] < INFINITY) && (Tf[1] == Tf[1]);
+          finite = (Tf[0] < INFINITY) && (Tf[2] < INFINITY) && (Pd == Pd);
           umax = wmaxf + sqrtf(Tf[4]);
           P = Tf[1];
           F2 = Tf[2];
@@ -927,7 +943,7 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
         c.ratio = 0.0;
         c.keep = 1.0;
         if (c.move) {
-          if (was64 ? (T[1] >= 0.0) : (P >= 0.0f)) {
+          if (was64 ? (T[1] >= 0.0) : (Pd >= 0.0)) {  // the FIRE power's sign, FP64
             npos++;
             if (npos > fp.n_min) {
               dtf = fminf(dtf * f_incf, dt_maxf);

@@ -14,14 +14,15 @@
 //
 // The scratch array is a file-scope __device__ variable: every GPU that loads
 // the library holds its 8 KiB until the process exits.  In host code its name
-// is only a host-side stand-in, never a device address, so the device address
-// is looked up once per device with cudaGetSymbolAddress (on the first call on
-// that device, with that device current) and passed to the kernels.
+// is only a host-side stand-in, never a device address, so every call looks
+// up the device address with cudaGetSymbolAddress in the caller's current
+// context and passes it to the kernels.  The address belongs to a context, not
+// to a device number (a reset device or another context has its own copy), so
+// it is not cached; the lookup is a cheap host call.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
-#include <mutex>
 
 #include "aqs_internal.cuh"
 #include "launch.cuh"
@@ -127,26 +128,10 @@ __global__ void k_energy_finish(const double* __restrict__ partial, int nblocks,
   energy_tau[1] = 0.5 * w * inv_vol;
 }
 
-// Device address of g_noalloc_partial, looked up once per device.
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[256];
-static bool g_noalloc_ready[256];
-
+// Device address of g_noalloc_partial in the current context.
 static cudaError_t noalloc_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ready[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_partial);
-    if (e != cudaSuccess) return e;
-    g_noalloc_addr[dev] = p;
-    g_noalloc_ready[dev] = true;
-  }
-  *out = g_noalloc_addr[dev];
-  return cudaSuccess;
+  *out = nullptr;
+  return cudaGetSymbolAddress(out, g_noalloc_partial);
 }
 
 }  // namespace aqs
@@ -193,13 +178,15 @@ extern "C" aqs_status aqs_energy_forces_noalloc(int dim, int64_t n, const double
       rcmax = std::fmax(rcmax, rc);
     }
   for (int k = 0; k < 9; k++) cf.H[k] = k < dim * dim ? box[k] : 0.0;
-  // upper-triangular cell with positive diagonal; the cutoff below half of the
-  // smallest perpendicular width (simple-shear tilt only)
+  // upper-triangular cell with positive diagonal and a tilt in H[0][1] only
+  // (the width test below and the minimum image assume it); the cutoff below
+  // half of the smallest perpendicular width
   for (int a = 0; a < dim; a++) {
     if (!(box[a * dim + a] > 0.0)) return AQS_ERR_INVALID_ARG;
     for (int b = 0; b < a; b++)
       if (box[a * dim + b] != 0.0) return AQS_ERR_INVALID_ARG;
   }
+  if (dim == 3 && (box[2] != 0.0 || box[5] != 0.0)) return AQS_ERR_INVALID_ARG;
   const double ly = box[1 * dim + 1], t = box[0 * dim + 1];
   double wmin = std::fmin(box[0] / std::sqrt(1.0 + (t / ly) * (t / ly)), ly);
   if (dim == 3) wmin = std::fmin(wmin, box[8]);

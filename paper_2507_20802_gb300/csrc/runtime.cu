@@ -27,6 +27,15 @@
 namespace aqs {
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n;
+}
 static thread_local std::string g_err;
 static std::atomic<int> g_timing{0};
 static aqs_kernel_stats g_stats{};
@@ -193,16 +202,13 @@ void cell_widths(int D, const double* H, double* w) {
   if (D == 3) w[2] = H[8];
 }
 
-// Cluster size for R replicas of n atoms: the largest C for which all R
-// clusters are resident at once (so every chain advances in every wave);
-// otherwise the C with the most resident CTAs.  At least 32 atoms per CTA and
-// at most 4096.
 // Cluster size for R concurrently minimised replicas of n atoms: spread the
-// replicas over the 152 SMs (one CTA per SM), at most 16 CTAs per replica, at
-// least 32 atoms per CTA and at most 4096.  The cluster scheduler's own limit
-// is checked with the occupancy API; a size it cannot place is skipped.
+// replicas over the device's SMs (one CTA per SM), at most 16 CTAs per
+// replica, at least 32 atoms per CTA and at most 4096.  The cluster
+// scheduler's own limit is checked with the occupancy API; a size it cannot
+// place is skipped.
 int auto_cluster(int dim, bool mixed, int R, int64_t n, int nt, int cap) {
-  int C = std::min(kMaxCluster, std::max(1, 152 / std::max(1, R)));
+  int C = std::min(kMaxCluster, std::max(1, sm_count() / std::max(1, R)));
   C = (int)std::min<int64_t>(C, std::max<int64_t>(1, n / 32));
   while ((n + C - 1) / C > 4096 && C < kMaxCluster) C++;
   for (; C > 1; C--) {
@@ -881,11 +887,26 @@ aqs_status check_box(aqs_system* s, int r, const double* H) {
 }
 
 // Copy user-order positions (host or device) of replica r into the system.
+// Non-finite coordinates are refused (AQS_ERR_NONFINITE) before anything is
+// written; device inputs are checked on a host copy.
 aqs_status put_positions(aqs_system* s, int r, const double* pos) {
   const int D = s->dim;
-  size_t bytes = sizeof(double) * D * s->n[r];
+  const size_t cnt = (size_t)D * s->n[r];
+  size_t bytes = sizeof(double) * cnt;
   const double* src = pos;
-  if (!is_device_ptr(pos)) {
+  const bool dev = is_device_ptr(pos);
+  std::vector<double> hcopy;
+  const double* hp = pos;
+  if (dev) {
+    hcopy.resize(cnt);
+    CUDA_TRY(cudaMemcpyAsync(hcopy.data(), pos, bytes, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    hp = hcopy.data();
+  }
+  for (size_t k = 0; k < cnt; k++)
+    if (!std::isfinite(hp[k]))
+      return fail(AQS_ERR_NONFINITE, "replica %d: position component %zu is not finite", r, k);
+  if (!dev) {
     CUDA_TRY(cudaMemcpyAsync(s->ubuf, pos, bytes, cudaMemcpyHostToDevice, s->stream));
     src = s->ubuf;
   }
@@ -1561,7 +1582,7 @@ struct aqs_warm {
   uint8_t* d_mask = nullptr;
   float* d_grad = nullptr;
   float* d_loss = nullptr;
-  int gblocks = 152;
+  int gblocks = 0;  // gradient partials: one per SM of the device
   int64_t adam_t = 0;
   std::vector<void*> allocs;
 };
@@ -1831,6 +1852,7 @@ aqs_status aqs_warm_create(int dim, int n_types, uint64_t seed, void* stream, aq
   w->dim = dim;
   w->n_types = n_types;
   w->stream = (cudaStream_t)stream;
+  w->gblocks = sm_count();
   aqs_status st = AQS_OK;
   __nv_bfloat16* wbf = nullptr;
   if ((st = walloc(w, &wbf, kNumWeights)) != AQS_OK ||

@@ -609,7 +609,7 @@ cudaError_t launch_mlp_forward(const MlpDev& m, const __nv_bfloat16* X, int64_t 
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (rows + 15) / 16;
-  int blocks = (int)std::min<int64_t>((ntiles + kInferWarps - 1) / kInferWarps, 152);
+  int blocks = (int)std::min<int64_t>((ntiles + kInferWarps - 1) / kInferWarps, sm_count());
   if (blocks < 1) blocks = 1;
   count_launch();
   k_mlp_infer<<<blocks, kInferWarps * 32, smem, s>>>(m, X, rows, Y, nout);

@@ -14,8 +14,18 @@ Each file is an .npz of FP64/int arrays:
   observables, decision log, final positions.
 * pardynk_2d_n256_s0.npz -- the same Algorithm-1 run with dynamic K
   (K_max = 12): chain length per pass, decisions, observables.
-* aqs_3d_n2048_s0.npz -- three sequential AQS steps of the 3D glass,
+* par_2d_n1024_s0.npz -- Algorithm 1 at the benchmark's shape, reduced:
+  the N = 1024 glass, dgamma = 1e-4, K = 10, P = 4, 400 steps (to
+  gamma = 0.04): per-step observables, decision log, final positions.
+* aqs_3d_n2048_s0.npz -- ten sequential AQS steps of the 3D glass,
   dgamma = 5e-5.
+* hist_2d_n256_s0.npz -- AQS under a deformation history on the N = 256
+  glass: 40 pull-push increments F = [[1, 2e-4], [1.5e-4, 1]] (Sec. 2.2),
+  then 40 increments of F^-1 (a strain cycle, Sec. 5): the history, per-step
+  observables, final positions, stored and laboratory cells.
+* parhist_2d_n256_s0.npz -- Algorithm 1 under the pull-push history
+  F = [[1, 4e-3], [3e-3, 1]], K = 3, P = 4, 24 steps: decision log and
+  per-step observables.
 * glass_sl_n400_s0.npz, aqs_sl_n400_s0.npz -- the paper's S/L glass (N = 400,
   density 1, Sec. 2.2) quenched by the oracle, and 20 sequential AQS steps
   of the paper's increment dgamma = 1/200 (Sec. 4).
@@ -93,11 +103,41 @@ def job_pardynk2d256():
              K_max=K_max, eq_tol=1e-6, **r)
 
 
+def job_par2d1024():
+    g = glass(2, 1024, 0)
+    dg, K, P, n = 1e-4, 10, 4, 400
+    r = oracle.parallel(_pot(2), _fire(), g["x"], g["types"], g["H"], dg, K, P, n, eq_tol=1e-6,
+                        n_threads=4)
+    assert r["status"] == 0
+    np.savez(os.path.join(HERE, "par_2d_n1024_s0.npz"), dgamma=dg, K=K, P=P, n_steps=n,
+             eq_tol=1e-6, **r)
+
+
 def job_aqs3d2048():
     g = glass(3, 2048, 0)
-    r = oracle.aqs(_pot(3), _fire(), g["x"], g["types"], g["H"], 5e-5, 3)
+    r = oracle.aqs(_pot(3), _fire(), g["x"], g["types"], g["H"], 5e-5, 10)
     assert r["status"] == 0
-    np.savez(os.path.join(HERE, "aqs_3d_n2048_s0.npz"), dgamma=5e-5, n_steps=3, **r)
+    np.savez(os.path.join(HERE, "aqs_3d_n2048_s0.npz"), dgamma=5e-5, n_steps=10, **r)
+
+
+def job_hist2d256():
+    g = glass(2, 256, 0)
+    F = np.array([[1.0, 2e-4], [1.5e-4, 1.0]])
+    hist = np.concatenate([np.tile(F, (40, 1, 1)), np.tile(np.linalg.inv(F), (40, 1, 1))])
+    r = oracle.aqs_history(_pot(2), _fire(), g["x"], g["types"], g["H"], hist)
+    assert r["status"] == 0
+    np.savez(os.path.join(HERE, "hist_2d_n256_s0.npz"), F_steps=hist, n_steps=len(hist), **r)
+
+
+def job_parhist2d256():
+    g = glass(2, 256, 0)
+    K, P, n = 3, 4, 24
+    hist = np.tile(np.array([[1.0, 4e-3], [3e-3, 1.0]]), (n, 1, 1))
+    r = oracle.parallel(_pot(2), _fire(), g["x"], g["types"], g["H"], 0.0, K, P, n, eq_tol=1e-6,
+                        n_threads=4, F_steps=hist)
+    assert r["status"] == 0
+    np.savez(os.path.join(HERE, "parhist_2d_n256_s0.npz"), F_steps=hist, K=K, P=P, n_steps=n,
+             eq_tol=1e-6, **r)
 
 
 def _pot_sl():

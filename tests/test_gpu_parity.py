@@ -135,6 +135,39 @@ def test_sequential_aqs_trajectory_matches_golden(A, syn, glass256, prec):
     np.testing.assert_allclose(s.box(), gold["H"], rtol=1e-12)
 
 
+def test_mixed_precision_fire_control_effect(A, syn, glass256):
+    """What mixed precision does to FIRE itself, on the 200-step oracle run.
+    In FP32 iterations the velocity update, dt and alpha run in FP32 and the
+    mixing norms |F|^2, |v|^2 in float-float sums, while the power P = F.v,
+    whose sign resets FIRE, is summed in FP64 and every convergence test is
+    FP64.  FP64 mode follows the oracle's FIRE iteration for iteration; mixed
+    mode follows the same minima (energies 1e-6, identical events) with
+    iteration counts that differ from step to step by roundoff-driven
+    divergence of the FIRE paths, but not in total."""
+    gold = load_golden("aqs_2d_n256_s0.npz")
+    x, t, H = glass256["x"], glass256["types"], glass256["H"]
+    n = int(gold["n_steps"])
+    it = {}
+    for prec in ("fp64", "mixed"):
+        s = make_system(A, syn, x, t, H, A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED)
+        out = s.run_sequential(float(gold["dgamma"]), n)
+        it[prec] = out["iters"][:, 0].astype(float)
+        assert np.array_equal(out["D"][:, 0] > EV_THR, gold["D"] > EV_THR)
+        s.close()
+    g = gold["iters"].astype(float)
+    stats = {}
+    for prec in ("fp64", "mixed"):
+        rel = (it[prec] - g) / g
+        stats[prec] = (it[prec].sum() / g.sum() - 1.0, np.median(np.abs(rel)), np.abs(rel).max())
+        print(f"{prec} FIRE iterations vs oracle: total {100 * stats[prec][0]:+.3f} %, per step "
+              f"median |.| {100 * stats[prec][1]:.3f} %, max |.| {100 * stats[prec][2]:.2f} %")
+    # FP64 mode: the oracle's FIRE up to the order of the force sums (a few
+    # iterations in the tail of a minimisation, < 2 % of a step)
+    assert abs(stats["fp64"][0]) < 0.005 and stats["fp64"][2] < 0.02
+    # mixed mode: FP32 FIRE control moves single steps, not the total
+    assert abs(stats["mixed"][0]) < 0.05 and stats["mixed"][1] < 0.05
+
+
 # ------------------------------------------------------------ Algorithm 1
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_parallel_stepping_matches_golden(A, syn, glass256, prec):

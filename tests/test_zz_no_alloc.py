@@ -43,6 +43,16 @@ def _noalloc(A, torch, syn, x, t, H):
     return float(e), out_f.cpu().numpy(), float(tau)
 
 
+def _check_cases(A, torch, syn, cases):
+    for x, t, H in cases:
+        E, F, tau = _regular(A, syn, x, t, H)
+        En, Fn, taun = _noalloc(A, torch, syn, x, t, H)
+        scale = max(1.0, np.abs(F).max())
+        assert En == pytest.approx(E, rel=1e-11, abs=1e-9)
+        assert np.abs(Fn - F).max() <= 1e-11 * scale
+        assert taun == pytest.approx(tau, rel=1e-10, abs=1e-10)
+
+
 def test_noalloc_energy_forces_match_regular_path_twice():
     torch = pytest.importorskip("torch")
     from paper_2507_20802_gb300 import aqs as A, synthetic as syn
@@ -52,13 +62,38 @@ def test_noalloc_energy_forces_match_regular_path_twice():
     H2 = H2.copy()
     H2[0, 1] = 0.03 * H2[1, 1]
     cases.append((x2, t2, H2))
-    for x, t, H in cases:
-        E, F, tau = _regular(A, syn, x, t, H)
-        En, Fn, taun = _noalloc(A, torch, syn, x, t, H)
-        scale = max(1.0, np.abs(F).max())
-        assert En == pytest.approx(E, rel=1e-11, abs=1e-9)
-        assert np.abs(Fn - F).max() <= 1e-11 * scale
-        assert taun == pytest.approx(tau, rel=1e-10, abs=1e-10)
+    _check_cases(A, torch, syn, cases)
+
+
+def test_noalloc_3d_tilted_glass_and_full_scratch():
+    """The 3D kernel on the stored 3D glass with an xy tilt, then the largest
+    size the fixed scratch takes (65 536 atoms: every slot of the array is
+    written and read), then the 3D glass again on the scratch the large call
+    left behind."""
+    torch = pytest.importorskip("torch")
+    from paper_2507_20802_gb300 import aqs as A, synthetic as syn
+    g = load_golden("glass_3d_n2048_s0.npz")
+    H3 = g["H"].copy()
+    H3[0, 1] = 0.02 * H3[1, 1]
+    x4, t4, H4 = syn.random_glass_start(65536, 2, seed=5)
+    _check_cases(A, torch, syn, [(g["x"], g["types"], H3), (x4, t4, H4),
+                                 (g["x"], g["types"], H3)])
+
+
+def test_noalloc_rejects_tilts_outside_xy():
+    """The 3D width test and minimum image assume the only tilt is H[0][1];
+    an xz or yz tilt is refused before anything is launched."""
+    pytest.importorskip("torch")
+    from paper_2507_20802_gb300 import aqs as A, synthetic as syn
+    pot = A.make_potential(syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR)
+    for k in (2, 5):
+        box = np.eye(3) * 20.0
+        box.flat[k] = 1.0
+        box = np.ascontiguousarray(box)
+        st = A.lib().aqs_energy_forces_noalloc(3, 100, C.c_void_p(1), C.c_void_p(1),
+                                               box.ctypes.data_as(C.POINTER(C.c_double)),
+                                               C.byref(pot), C.c_void_p(1), C.c_void_p(1), None)
+        assert st == A.AQS_ERR_INVALID_ARG
 
 
 def test_noalloc_rejects_sizes_beyond_the_scratch():
