@@ -572,6 +572,139 @@ def run_glass3d(args):
                       "cluster_size": b.cluster_size(0), "staging": b.staging(0)}})
 
 
+def quench_3d(A, syn, n, seed, max_iter):
+    """The 3D glass of the cfg3 workload: seeded random start, mixed-precision
+    GPU FIRE quench (status and iterations returned; not converged when the
+    budget runs out)."""
+    x, t, H = syn.random_glass_start(n, 3, seed=seed)
+    s = A.System(x, t, H[None], [n], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
+                 precision=A.AQS_MIXED)
+    q = s.minimize(A.fire_params(max_iter=max_iter), check_status=False)[0]
+    xq, Hq = s.positions(), s.box()
+    s.close()
+    return xq, t, Hq, q
+
+
+def run_cfg3(args):
+    """Algorithm 1 in 3D (80:20 binary LJ glass, N = 65536, density 1.2): P = 32
+    chains of K = 20 fine steps of dgamma = 5e-5, every step converged to
+    |F|max < 1e-10 (FP64 test), mixed precision; `steps` passes after
+    `warmup` passes, from the quenched glass.  value = accepted fine steps /
+    s (device time).  The plain FP64 sequential GPU AQS on the same glass
+    (same kernels in FP64 mode, one replica) runs `baseline_steps` steps
+    from the r_star reached."""
+    import torch
+    from paper_2507_20802_gb300 import aqs as A, synthetic as syn
+    torch.cuda.set_device(0)
+    n, P, K, dg = 65536, 32, 20, 5e-5
+    t0 = time.perf_counter()
+    xq, t, Hq, q = quench_3d(A, syn, n, 0, args.quench_iters)
+    quench_s = time.perf_counter() - t0
+    assert q["status"] == 0, q
+    s = A.System(xq, t, Hq[None], [n], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
+                 precision=A.AQS_MIXED)
+    s.set_launch_budget(args.launch_budget)
+    n_total = int(round(0.15 / dg))
+    done = 0
+
+    def one_pass():
+        nonlocal done
+        r = s.parallel_step(dg, K, P, max(1, n_total - done), max_iterations=1)
+        done += r["accepted"]
+        return r
+    for _ in range(args.warmup):
+        one_pass()
+    A.aqs_reset_kernel_stats()
+    A.aqs_set_kernel_timing(True)
+    l0 = A.aqs_launch_count()
+    acc, ms, rej, passes = 0, 0.0, 0, []
+    with Clocks(0) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = one_pass()
+            e1.record()
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            acc += r["accepted"]
+            rej += r["rejections"]
+            passes.append({"accepted": int(r["accepted"]), "ms": e0.elapsed_time(e1),
+                           "fire_iters_total": int(r["fire_iters_total"]),
+                           "first_failed_chain": int(r["log_i"][r["log_eq"] == 0][0])
+                           if np.any(r["log_eq"] == 0) else None})
+    st = A.aqs_get_kernel_stats()
+    A.aqs_set_kernel_timing(False)
+    value = acc / (ms / 1e3)
+    base = None
+    if args.baseline_steps > 0:
+        b = A.System(s.positions(), t, s.box()[None], [n], syn.LJ_SIGMA, syn.LJ_EPS,
+                     syn.RC_FACTOR, precision=A.AQS_FP64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ob = b.run_sequential(dg, args.baseline_steps)
+        e1.record()
+        e1.synchronize()
+        bs = e0.elapsed_time(e1) / 1e3
+        base = {"value": args.baseline_steps / bs, "unit": UNIT, "steps": args.baseline_steps,
+                "fire_iters_per_step": float(ob["iters"].mean()),
+                "speedup_of_value": value / (args.baseline_steps / bs),
+                "cluster_size": b.cluster_size()}
+        b.close()
+    kern_s = st["kernel_ms"] / 1e3
+    algo_bytes = 4.0 * st["pairs32"] + 28.0 * n * st["evals32"]
+    gbs = algo_bytes / kern_s / 1e9 if kern_s else 0.0
+    peak = _peaks().get("hbm_gbs", 6800.0)
+    config = {"workload": "3D binary LJ glass (80:20, rho=1.2), N=65536, Algorithm 1 with P=32 "
+                          "chains of K=20 fine steps, dgamma=5e-5, FIRE to |F|max<1e-10, mixed "
+                          "precision", "n_atoms": n, "P": P, "K": K, "dgamma": dg,
+              "l2": "lists of the chains (~1 GB) exceed L2"}
+    _line(METRIC + " (3D)", value, UNIT, args, ms / max(1, args.steps), config,
+          {"gpu_launches": A.aqs_launch_count() - l0, "clocks": clk.summary(),
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                        "frac": gbs / peak, "traffic": None,
+                        "note": "algorithmic bytes = 4 per list entry visited + 28 per atom per "
+                                "FP32 evaluation, over all minimiser launches of the passes"},
+           "fp64_sequential_gpu_baseline": base,
+           "detail": {"accepted_steps": acc, "rejections": rej, "passes": passes,
+                      "quench_iters": q["iters"], "quench_s": quench_s,
+                      "fire_iters_per_step": float(np.mean([p["fire_iters_total"] for p in passes]))
+                      / max(1, acc / max(1, len(passes))),
+                      "fp32_evals": st["evals32"], "fp64_evals": st["evals64"]}})
+
+
+def force_3d_line(A, syn, quench_iters, replicas, iters):
+    """Force-kernel bandwidth on the 3D workload for the default line: the
+    cfg3 glass (partially quenched within `quench_iters`), `replicas` copies at
+    the level-II fine steps, `iters` FIRE iterations each, timed by CUDA
+    events in the library."""
+    n, dg = 65536, 5e-5
+    xq, t, Hq, q = quench_3d(A, syn, n, 0, quench_iters)
+    b = A.System(np.tile(xq, (replicas, 1)), np.tile(t, replicas),
+                 np.tile(Hq[None], (replicas, 1, 1)), [n] * replicas, syn.LJ_SIGMA, syn.LJ_EPS,
+                 syn.RC_FACTOR, precision=A.AQS_MIXED)
+    b.shear((np.arange(replicas) + 1) * dg)
+    b.minimize(A.fire_params(max_iter=50), check_status=False)
+    A.aqs_reset_kernel_stats()
+    A.aqs_set_kernel_timing(True)
+    b.minimize(A.fire_params(max_iter=iters), check_status=False)
+    st = A.aqs_get_kernel_stats()
+    A.aqs_set_kernel_timing(False)
+    b.close()
+    kern_s = st["kernel_ms"] / 1e3
+    algo_bytes = 4.0 * st["pairs32"] + 28.0 * n * st["evals32"]
+    gbs = algo_bytes / kern_s / 1e9 if kern_s else 0.0
+    peak = _peaks().get("hbm_gbs", 6800.0)
+    return {"kernel": "k_minimize<3,mixed> (lean launch)", "bound": "hbm", "achieved": gbs,
+            "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "workload": "3D glass N=65536 (quench budget %d iterations, fmax %.2g), %d replicas "
+                        "at fine steps of 5e-5, %d FIRE iterations each"
+                        % (quench_iters, q["fmax"], replicas, iters),
+            "algorithmic_bytes": "4 per list entry visited + 28 per atom per FP32 evaluation",
+            "kernel_ms": st["kernel_ms"], "fp32_evals": st["evals32"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -584,8 +717,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--baseline-steps", type=int, default=20)
-    ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d", "warm", "oracle-threads"],
-                    default="cfg1")
+    ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d", "cfg3", "warm",
+                                           "oracle-threads"], default="cfg1")
+    ap.add_argument("--no-force3d", action="store_true",
+                    help="skip the 3D force-kernel bandwidth figure of the default line")
     ap.add_argument("--oracle-steps", type=int, default=60)
     ap.add_argument("--oracle-P", type=int, nargs="+", default=[4, 8, 16])
     ap.add_argument("--oracle-K", type=int, nargs="+", default=[1, 10])
@@ -613,6 +748,8 @@ def main():
         return run_glass3d(args) or 0
     if args.workload == "oracle-threads":
         return run_oracle_threads(args) or 0
+    if args.workload == "cfg3":
+        return run_cfg3(args) or 0
 
     import torch
     ws, rank, local = _dist()
@@ -789,6 +926,11 @@ def main():
                 "speedup_of_value": value / bval,
                 "speedup_same_steps": value / same}
 
+    # ---------------- the force kernel's HBM bandwidth on the 3D workload
+    force3d = None
+    if rank == 0 and not args.no_force3d:
+        force3d = force_3d_line(A, syn, 20000, 32, 500)
+
     # ---------------- CPU baseline (oracle, rank 0, N = 1 only)
     cpu = None
     mean_iters = float(np.mean(iters)) if iters else float("nan")
@@ -812,6 +954,7 @@ def main():
                 "gpu_launches": int(gpu_launches), "clocks": clocks, "roofline": roofline,
                 "cpu_baseline": cpu,
                 "fp64_sequential_gpu_baseline": base,
+                "force_kernel_3d": force3d,
                 "detail": {"accepted_steps": int(total_steps), "rejections": rej,
                            "chains_stopped_early": stopped, "autotune_iters": args.autotune,
                            "launch_budget": args.launch_budget, "k_max": args.k_max,

@@ -187,6 +187,15 @@ typedef struct {
                              failed test and max(1, ceil(q / P)) after one, q the
                              steps that pass accepted; <= K keeps K fixed.  The
                              trajectory is that of sequential AQS either way. */
+  const double* F_steps;  /* nullable: a deformation history for this call,
+                             host [n_steps][dim][dim] (see aqs_run_history);
+                             fine step k applies F_steps[k] instead of the
+                             simple shear by dgamma, and level I maps chain i
+                             by the i K increments that follow the current
+                             step, one after the other (for simple shear this
+                             is the paper's F^(i K dgamma); for a general
+                             history it keeps chain i's start in the cell where
+                             chain i-1 ends).  Not with warm_start. */
 } aqs_parallel_params;
 
 typedef struct {
@@ -218,6 +227,32 @@ typedef struct {
 
 aqs_status aqs_parallel_step(aqs_system* sys, int replica, const aqs_fire_params* fire,
                              const aqs_parallel_params* params, aqs_parallel_result* out);
+
+/* ---- general deformation histories ----
+ * The paper's protocol uses simple shear (Eq. 16) and states that the method
+ * works as well for pull-push ("pure") shear F = [[1, dg_x], [dg_y, 1]]
+ * (Sec. 2.2) and for other deformation histories such as cyclic protocols
+ * (Sec. 5).  An increment F (d x d, row-major) acts on the laboratory cell:
+ * H_lab <- F H_lab, r <- F r (Eqs. 1-3).  The library keeps every cell upper
+ * triangular: it stores H = Q^T H_lab with Q the Gram-Schmidt frame of H_lab
+ * (aqs_get_frame) and the configuration in that frame, so stored positions
+ * move by the upper-triangular map Q_new^T F Q_old.  For simple shear Q stays
+ * the identity.  3D histories must keep the stored cell tilted in xy only
+ * (AQS_ERR_UNSUPPORTED otherwise); every cell reached must satisfy the
+ * minimum-image rule (AQS_ERR_BOX_TOO_SMALL, nothing applied). */
+
+/* One increment per replica: F host [n_replicas][dim][dim].  Lists are
+ * rebuilt in the new cell. */
+aqs_status aqs_deform(aqs_system* sys, const double* F);
+/* Sequential AQS (Eq. 12) under a deformation history: step k applies
+ * F[k] (host [n_steps][dim][dim], the same history for every replica), then
+ * minimises.  Outputs as aqs_run_sequential. */
+aqs_status aqs_run_history(aqs_system* sys, const aqs_fire_params* fire, const double* F,
+                           int64_t n_steps, double* energy, double* tau, int64_t* fire_iters,
+                           double* nonaffine);
+/* Q (host [dim][dim], row-major): laboratory = Q x stored, for positions and
+ * cell; the identity unless a history rotated the cell. */
+aqs_status aqs_get_frame(const aqs_system* sys, int replica, double* Q);
 
 /* Equality test of Eq. 20 between replica ra of a and replica rb of b (same
  * atom count, same cell): max_disp = max_a |mi(r_a - r_b) - mean|,

@@ -60,7 +60,8 @@ class aqs_parallel_params(C.Structure):
     _fields_ = [("dgamma", C.c_double), ("K", C.c_int), ("P", C.c_int),
                 ("n_steps", C.c_int64), ("eq_tol", C.c_double),
                 ("event_threshold", C.c_double), ("max_iterations", C.c_int64),
-                ("warm_start", C.c_int), ("run_discarded", C.c_int), ("K_max", C.c_int)]
+                ("warm_start", C.c_int), ("run_discarded", C.c_int), ("K_max", C.c_int),
+                ("F_steps", C.POINTER(C.c_double))]
 
 
 class aqs_parallel_result(C.Structure):
@@ -96,6 +97,11 @@ _SIGS = {
     "aqs_parallel_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(aqs_fire_params),
                                     C.POINTER(aqs_parallel_params),
                                     C.POINTER(aqs_parallel_result)]),
+    "aqs_deform": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "aqs_run_history": (C.c_int, [C.c_void_p, C.POINTER(aqs_fire_params), C.POINTER(C.c_double),
+                                  C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "aqs_get_frame": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "aqs_compare_configs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double,
                                       C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "aqs_num_replicas": (C.c_int, [C.c_void_p]),
@@ -250,10 +256,14 @@ def aqs_run_sequential(h, fire, dgamma, n_steps, n_replicas):
 
 def aqs_parallel_step(h, replica, fire, dgamma, K, P, n_steps, eq_tol=1e-6,
                       event_threshold=1e-2, max_iterations=0, warm_start=0, log_cap=100000,
-                      run_discarded=0, K_max=0):
+                      run_discarded=0, K_max=0, F_steps=None):
     p = aqs_parallel_params(dgamma=dgamma, K=K, P=P, n_steps=n_steps, eq_tol=eq_tol,
                             event_threshold=event_threshold, max_iterations=max_iterations,
                             warm_start=warm_start, run_discarded=run_discarded, K_max=K_max)
+    Fh = None
+    if F_steps is not None:
+        Fh = np.ascontiguousarray(F_steps, dtype=np.float64)
+        p.F_steps = _dp(Fh)
     n = max(int(n_steps), 1)
     E, tau, D = np.zeros(n), np.zeros(n), np.zeros(n)
     it = np.zeros(n, dtype=np.int64)
@@ -281,6 +291,29 @@ def aqs_parallel_step(h, replica, fire, dgamma, K, P, n_steps, eq_tol=1e-6,
                 fire_iters_total=r.fire_iters_total, evals64_total=r.evals64_total,
                 chains_stopped=r.chains_stopped, K_pass=kp[:r.iterations], K_next=r.K_next,
                 log_iter=li[:nl], log_i=lc[:nl], log_eq=le[:nl], log_m=lm[:nl])
+
+
+def aqs_deform(h, F):
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    check(lib().aqs_deform(h, _dp(F)))
+
+
+def aqs_run_history(h, fire, F_steps, n_replicas):
+    F = np.ascontiguousarray(F_steps, dtype=np.float64)
+    n_steps = F.shape[0]
+    E = np.zeros((n_steps, n_replicas))
+    tau = np.zeros((n_steps, n_replicas))
+    it = np.zeros((n_steps, n_replicas), dtype=np.int64)
+    D = np.zeros((n_steps, n_replicas))
+    check(lib().aqs_run_history(h, C.byref(fire), _dp(F), C.c_int64(n_steps), _dp(E), _dp(tau),
+                                it.ctypes.data_as(C.POINTER(C.c_int64)), _dp(D)))
+    return dict(E=E, tau=tau, iters=it, D=D)
+
+
+def aqs_get_frame(h, replica, dim):
+    Q = np.zeros((dim, dim))
+    check(lib().aqs_get_frame(h, replica, _dp(Q)))
+    return Q
 
 
 def aqs_compare_configs(ha, ra, hb, rb, tol):
@@ -470,6 +503,16 @@ class System:
 
     def run_sequential(self, dgamma, n_steps, fire=None):
         return aqs_run_sequential(self.h, fire or fire_params(), dgamma, n_steps, self.R)
+
+    def run_history(self, F_steps, fire=None):
+        return aqs_run_history(self.h, fire or fire_params(), F_steps, self.R)
+
+    def deform(self, F):
+        F = np.broadcast_to(np.asarray(F, np.float64), (self.R, self.dim, self.dim))
+        aqs_deform(self.h, F)
+
+    def frame(self, replica=0):
+        return aqs_get_frame(self.h, replica, self.dim)
 
     def parallel_step(self, dgamma, K, P, n_steps, fire=None, replica=0, **kw):
         return aqs_parallel_step(self.h, replica, fire or fire_params(), dgamma, K, P, n_steps,

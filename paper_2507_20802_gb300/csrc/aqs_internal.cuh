@@ -69,7 +69,15 @@ struct RepState {
   int first_noaffine;
   int want_snap;    // write the positions after the first (no-affine) step
   int kreb;         // Verlet rebuilds done inside the kernel (monotonic)
+  // Deformation histories (launches with a map table): the current cell,
+  // authoritative while such a job runs, and the cell at the last list build.
+  double Hc[9];
+  double Hb[9];
 };
+
+// Deformation-history table: per replica and job step, the map M of stored
+// positions (upper triangular, row-major 3 x 3 slots) and the new stored cell.
+constexpr int kHistFields = 18;
 
 // per converged step the kernel records: E, tau, D_k (from the affine start), FIRE
 // iterations, FP64 evaluations, max displacement from the minimisation's start
@@ -122,6 +130,28 @@ __host__ __device__ inline void cell_origin(const double* H, const int* nc, int 
     for (int k = r; k < D; k++) s += H[r * D + k] * f[k];
     o[r] = s;
   }
+}
+
+// Frobenius norm of H Hb^-1 - I for upper-triangular cells: the largest
+// relative change (bound) of any separation vector under the affine maps
+// applied since the cell was Hb.  For simple shear it is |dt| / L_y.
+template <int D>
+__host__ __device__ inline double affine_change(const double* H, const double* Hb) {
+  double A[9];
+  // A Hb = H, column by column (Hb upper triangular)
+  for (int c = 0; c < D; c++)
+    for (int r = 0; r < D; r++) {
+      double v = H[r * D + c];
+      for (int k = 0; k < c; k++) v -= A[r * D + k] * Hb[k * D + c];
+      A[r * D + c] = v / Hb[c * D + c];
+    }
+  double f = 0.0;
+  for (int r = 0; r < D; r++)
+    for (int c = 0; c < D; c++) {
+      const double e = A[r * D + c] - (r == c ? 1.0 : 0.0);
+      f += e * e;
+    }
+  return sqrt(f);
 }
 
 // Minimum image of a separation d under the upper-triangular cell H: remove

@@ -49,6 +49,11 @@ struct MinArgs {
   // [3][ntot] FP64 force
   float* lean32;
   double* lean64;
+  // deformation history (nullable): [R][hist_stride][kHistFields], the map
+  // and cell of every job step (step 0 of a no-affine job unused); with it
+  // the kernel keeps the full cell in RepState::Hc / Hb
+  const double* hist;
+  int64_t hist_stride;
 };
 
 // Staging modes of the minimiser (where a CTA finds list rows and the

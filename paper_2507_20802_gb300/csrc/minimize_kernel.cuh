@@ -241,10 +241,13 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
   __syncthreads();
 
   // ---- set-up: geometry (tilt from the kernel-written state), tables ----
-  double H[9];
+  double H[9], Hb[9];
+  const bool HIST = A.hist != nullptr;  // uniform: a launch has a table or not
 #pragma unroll
-  for (int k = 0; k < 9; k++) H[k] = g.H[k];
-  H[1] = st->tilt;
+  for (int k = 0; k < 9; k++) H[k] = HIST ? st->Hc[k] : g.H[k];
+  if (!HIST) H[1] = st->tilt;
+#pragma unroll
+  for (int k = 0; k < 9; k++) Hb[k] = HIST ? st->Hb[k] : 0.0;
   const int ncode = D == 2 ? 9 : 27;
   auto make_tables = [&]() {
     if (tid < ncode) {
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
   int64_t launch_iters = 0;
   int64_t acc_it = st->acc_iters, acc64 = st->acc64, acc32 = st->acc32;
   int kreb = st->kreb;
-  const double vol = D == 2 ? H[0] * H[3] : H[0] * H[4] * H[8];
+  double vol = D == 2 ? H[0] * H[3] : H[0] * H[4] * H[8];
   bool want_e = MIXED;  // mixed: every FP64 evaluation also gives E and tau
   float wmaxf = 0.0f;   // max |x_ref - x_b| at the last FP64 evaluation (mixed)
   // mixed: true while A.v holds the current velocity in FP64 (moves after FP64
@@ -635,7 +638,20 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
         int li = tid + k * nthr;
         if (li >= cnt) continue;
         int64_t gi = base + li;
-        if (affine) {
+        if (affine && HIST) {
+          // deformation history: x <- M x (upper triangular), the list-build
+          // positions alike
+          const double* M = A.hist + ((int64_t)ri * A.hist_stride + step) * kHistFields;
+          for (int a = 0; a < D; a++) {
+            double xa = M[a * 3 + a] * A.x[a * N + gi], ba = M[a * 3 + a] * A.xb[a * N + gi];
+            for (int c = a + 1; c < D; c++) {
+              xa = fma(M[a * 3 + c], A.x[c * N + gi], xa);
+              ba = fma(M[a * 3 + c], A.xb[c * N + gi], ba);
+            }
+            A.x[a * N + gi] = xa;
+            A.xb[a * N + gi] = ba;
+          }
+        } else if (affine) {
           A.x[gi] = fma(dgam, A.x[N + gi], A.x[gi]);
           A.xb[gi] = fma(dgam, A.xb[N + gi], A.xb[gi]);
           if (A.warm_u) {
@@ -651,7 +667,14 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
           Dl(k, c) = 0.0f;
         }
       }
-      if (affine) H[1] = fma(dgam, H[D + 1], H[1]);
+      if (affine && HIST) {
+        const double* Hn = A.hist + ((int64_t)ri * A.hist_stride + step) * kHistFields + 9;
+        for (int a = 0; a < D; a++)
+          for (int c = 0; c < D; c++) H[a * D + c] = Hn[a * 3 + c];
+        vol = D == 2 ? H[0] * H[3] : H[0] * H[4] * H[8];
+      } else if (affine) {
+        H[1] = fma(dgam, H[D + 1], H[1]);
+      }
       dt = fp.dt0;
       alpha = fp.alpha0;
       dtf = (float)dt;
@@ -663,7 +686,7 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
       phase = 1;
       make_tables();
     }
-    gamma_term = fabs(H[1] - tilt_b) / H[D + 1] * A.rlist;
+    gamma_term = HIST ? affine_change<D>(H, Hb) * A.rlist : fabs(H[1] - tilt_b) / H[D + 1] * A.rlist;
     gamma_termf = (float)gamma_term;
 #pragma unroll
     for (int k = 0; k < APT; k++)
@@ -1194,6 +1217,8 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
       if (rebuild_lists()) {
         kreb++;
         tilt_b = H[1];
+#pragma unroll
+        for (int k = 0; k < 9; k++) Hb[k] = H[k];
         wmaxf = 0.0f;
         status = kStatusRunning;
         continue;  // republishes FP64 positions; the next evaluation is FP64
@@ -1301,6 +1326,11 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
     st->phase = phase;
     st->tilt = H[1];
     st->tilt_b = tilt_b;
+    if (HIST)
+      for (int k = 0; k < 9; k++) {
+        st->Hc[k] = H[k];
+        st->Hb[k] = Hb[k];
+      }
     if (status == AQS_OK) {
       st->E = E;
       st->tau = W;

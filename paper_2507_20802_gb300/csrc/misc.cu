@@ -31,24 +31,73 @@ cudaError_t launch_affine(double* x, double* xb, const int32_t* rep_of, const do
   return cudaGetLastError();
 }
 
+// Deformation-history increment (Eqs. 1-3 with a general matrix, expressed in
+// the frame where the cell stays upper triangular): r <- M r, r_b <- M r_b.
+// The diagonal term first, so that simple shear is the fma of k_affine.
+__device__ __forceinline__ void map_upper(int D, const double* M, const double* v, double* out) {
+  for (int a = 0; a < D; a++) {
+    double s = M[a * 3 + a] * v[a];
+    for (int c = a + 1; c < D; c++) s = fma(M[a * 3 + c], v[c], s);
+    out[a] = s;
+  }
+}
+
+__global__ void k_deform(int D, double* x, double* xb, const int32_t* rep_of, const uint8_t* flag,
+                         const double* maps, int64_t N) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int r = rep_of[i];
+  if (!flag[r]) return;
+  const double* M = maps + 9 * (int64_t)r;
+  double v[3], w[3];
+  for (int c = 0; c < D; c++) v[c] = x[c * N + i];
+  map_upper(D, M, v, w);
+  for (int c = 0; c < D; c++) x[c * N + i] = w[c];
+  for (int c = 0; c < D; c++) v[c] = xb[c * N + i];
+  map_upper(D, M, v, w);
+  for (int c = 0; c < D; c++) xb[c * N + i] = w[c];
+}
+
+cudaError_t launch_deform(int dim, double* x, double* xb, const int32_t* rep_of,
+                          const uint8_t* flag, const double* maps, int64_t N, cudaStream_t s) {
+  count_launch();
+  k_deform<<<nblk(N, 256), 256, 0, s>>>(dim, x, xb, rep_of, flag, maps, N);
+  return cudaGetLastError();
+}
+
 // Level I (Sec. 3.2, Eq. 18): copies of one replica, copy c sheared by
-// shift[c] (= c K dgamma), FIRE velocities cleared.
+// shift[c] (= c K dgamma), or mapped by maps[c] under a deformation history;
+// FIRE velocities cleared.
 __global__ void k_copy_rep(RepCopy a) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)a.ncopy * a.n) return;
   int c = (int)(idx / a.n);
   int p = (int)(idx % a.n);
   int64_t si = a.soff + p, di = a.doff[c] + p;
-  double g = a.shift[c];
-  for (int k = 0; k < a.D; k++) {
-    double xv = a.sx[k * a.sN + si], bv = a.sxb[k * a.sN + si];
-    if (k == 0 && g != 0.0) {
-      xv = fma(g, a.sx[a.sN + si], xv);
-      bv = fma(g, a.sxb[a.sN + si], bv);
+  if (a.maps) {
+    double v[3], w[3];
+    const double* M = a.maps + 9 * (int64_t)c;
+    for (int k = 0; k < a.D; k++) v[k] = a.sx[k * a.sN + si];
+    map_upper(a.D, M, v, w);
+    for (int k = 0; k < a.D; k++) a.dx[k * a.dN + di] = w[k];
+    for (int k = 0; k < a.D; k++) v[k] = a.sxb[k * a.sN + si];
+    map_upper(a.D, M, v, w);
+    for (int k = 0; k < a.D; k++) {
+      a.dxb[k * a.dN + di] = w[k];
+      a.dv[k * a.dN + di] = 0.0;
     }
-    a.dx[k * a.dN + di] = xv;
-    a.dxb[k * a.dN + di] = bv;
-    a.dv[k * a.dN + di] = 0.0;
+  } else {
+    double g = a.shift[c];
+    for (int k = 0; k < a.D; k++) {
+      double xv = a.sx[k * a.sN + si], bv = a.sxb[k * a.sN + si];
+      if (k == 0 && g != 0.0) {
+        xv = fma(g, a.sx[a.sN + si], xv);
+        bv = fma(g, a.sxb[a.sN + si], bv);
+      }
+      a.dx[k * a.dN + di] = xv;
+      a.dxb[k * a.dN + di] = bv;
+      a.dv[k * a.dN + di] = 0.0;
+    }
   }
   a.dtype[di] = a.stype[si];
   a.dperm[di] = a.sperm[si];

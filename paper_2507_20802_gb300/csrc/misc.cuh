@@ -16,6 +16,9 @@ struct RepCopy {
   const int64_t* doff;     // device [ncopy]
   const int64_t* dnb_off;  // device [ncopy]
   const double* shift;     // device [ncopy]
+  // device [ncopy][9] (nullable): instead of the shear shift, copy c is mapped
+  // by the upper-triangular matrix maps[c] (row-major 3 x 3 slots)
+  const double* maps;
   int n, cap, ncopy, D;
 };
 
@@ -46,6 +49,11 @@ struct EnergyArgs {
 cudaError_t launch_affine(double* x, double* xb, const int32_t* rep_of, const double* dg,
                           int64_t N, cudaStream_t s);
 cudaError_t launch_copy_rep(const RepCopy& a, cudaStream_t s);
+// General affine increment of a deformation history: atoms of replica r (and
+// their list-build positions) are mapped by the upper-triangular maps[r]
+// (device [R][9], row-major 3 x 3 slots); replicas with flag[r] == 0 untouched.
+cudaError_t launch_deform(int dim, double* x, double* xb, const int32_t* rep_of,
+                          const uint8_t* flag, const double* maps, int64_t N, cudaStream_t s);
 cudaError_t launch_gather_user(const double* x, int64_t N, int64_t off, int n, const int32_t* perm,
                                int D, double* out, cudaStream_t s);
 cudaError_t launch_scatter_user(const double* in, double* x, int64_t N, int64_t off, int n,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -137,6 +138,14 @@ struct aqs_system {
   float* d_u = nullptr;
   double* d_save = nullptr;
   int* d_err = nullptr;
+  // deformation histories: the rotation Q (row-major d x d) from the stored
+  // frame, where every cell is upper triangular, to the laboratory frame
+  // (H_lab = Q H); the identity unless a history rotated the cell
+  std::vector<std::array<double, 9>> frame;
+  double* d_hist = nullptr;  // [R][hist_cap][kHistFields] job map tables
+  int64_t hist_cap = 0;
+  double* d_maps = nullptr;  // [R][9] one-increment maps (aqs_deform, level I)
+  bool hist_launch = false;  // the running job set uses a map table
   // two-level stepping resources
   aqs_system* chains = nullptr;
   double* snap = nullptr;
@@ -236,18 +245,29 @@ aqs_status download_state(aqs_system* s) {
   CUDA_TRY(cudaStreamSynchronize(s->stream));
   // the kernels own the tilt while they shear; mirror it into the geometry
   bool changed = false;
-  for (int r = 0; r < s->R; r++)
-    if (s->geom[r].H[1] != s->st[r].tilt) {
+  for (int r = 0; r < s->R; r++) {
+    if (s->hist_launch) {
+      for (int k = 0; k < s->dim * s->dim; k++)
+        if (s->geom[r].H[k] != s->st[r].Hc[k]) {
+          s->geom[r].H[k] = s->st[r].Hc[k];
+          changed = true;
+        }
+    } else if (s->geom[r].H[1] != s->st[r].tilt) {
       s->geom[r].H[1] = s->st[r].tilt;
       changed = true;
     }
+    std::memcpy(s->st[r].Hc, s->geom[r].H, sizeof(s->st[r].Hc));
+  }
   if (changed) AQS_TRY(upload_geom(s));
   return AQS_OK;
 }
 
 // after the host changed a cell: the kernel-side copy of the tilt follows
 void sync_tilt_to_state(aqs_system* s) {
-  for (int r = 0; r < s->R; r++) s->st[r].tilt = s->geom[r].H[1];
+  for (int r = 0; r < s->R; r++) {
+    s->st[r].tilt = s->geom[r].H[1];
+    std::memcpy(s->st[r].Hc, s->geom[r].H, sizeof(s->st[r].Hc));
+  }
 }
 
 BuildArgs build_args(aqs_system* s) {
@@ -371,6 +391,8 @@ aqs_status rebuild(aqs_system* s, const std::vector<uint8_t>& flags, int depth =
       s->geom[r].tilt_b = s->geom[r].H[0 * D + 1];
       s->st[r].tilt_b = s->geom[r].tilt_b;
       s->st[r].tilt = s->geom[r].H[0 * D + 1];
+      std::memcpy(s->st[r].Hb, s->geom[r].H, sizeof(s->st[r].Hb));
+      std::memcpy(s->st[r].Hc, s->geom[r].H, sizeof(s->st[r].Hc));
     }
   AQS_TRY(upload_geom(s));
   AQS_TRY(upload_state(s));
@@ -465,6 +487,8 @@ MinArgs min_args(aqs_system* s, const aqs_fire_params* f) {
   a.pubg = s->pubg;
   a.lean32 = s->lean32;
   a.lean64 = s->lean64;
+  a.hist = nullptr;
+  a.hist_stride = 0;
   for (int k = 0; k < AQS_MAX_TYPES * AQS_MAX_TYPES; k++) a.rl2f[k] = s->rl2f[k];
   return a;
 }
@@ -503,6 +527,9 @@ struct Job {
   double dgamma = 0.0;
   int first_noaffine = 0;
   int want_snap = 0;
+  // deformation history: nsteps x kHistFields rows (map, new cell) per job
+  // step; empty = simple shear by dgamma
+  std::vector<double> table;
 };
 
 struct JobOut {
@@ -581,6 +608,46 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
     }
   if (todo.empty()) return AQS_OK;
   AQS_TRY(ensure_records(s, maxsteps, snap));
+  // deformation histories: every job of the set gets a table (jobs without
+  // one get the rows of their simple shear), uploaded [R][maxsteps][18]
+  bool any_table = false;
+  for (int r : todo) any_table = any_table || !jobs[r].table.empty();
+  s->hist_launch = any_table;
+  if (any_table) {
+    if (maxsteps > s->hist_cap) {
+      dfree(s, s->d_hist);
+      s->hist_cap = std::max<int64_t>(maxsteps, 2 * s->hist_cap);
+      AQS_TRY(alloc_arr(s, &s->d_hist, (size_t)s->R * s->hist_cap * kHistFields));
+    }
+    std::vector<double> all((size_t)s->R * s->hist_cap * kHistFields, 0.0);
+    for (int r : todo) {
+      double* dst = all.data() + (size_t)r * s->hist_cap * kHistFields;
+      if (!jobs[r].table.empty()) {
+        std::copy(jobs[r].table.begin(), jobs[r].table.end(), dst);
+        continue;
+      }
+      double H[9];
+      std::memcpy(H, s->geom[r].H, sizeof(H));
+      for (int64_t k = 0; k < jobs[r].nsteps; k++) {
+        double* row = dst + k * kHistFields;
+        for (int a = 0; a < 3; a++) row[a * 3 + a] = 1.0;
+        if (!(k == 0 && jobs[r].first_noaffine)) {
+          row[1] = jobs[r].dgamma;
+          H[1] = std::fma(jobs[r].dgamma, H[s->dim + 1], H[1]);
+        }
+        for (int a = 0; a < s->dim; a++)
+          for (int c = 0; c < s->dim; c++) row[9 + a * 3 + c] = H[a * s->dim + c];
+      }
+    }
+    CUDA_TRY(cudaMemcpyAsync(s->d_hist, all.data(), sizeof(double) * all.size(),
+                             cudaMemcpyHostToDevice, s->stream));
+    for (int r : todo) {
+      std::memcpy(s->st[r].Hc, s->geom[r].H, sizeof(s->st[r].Hc));
+      // a simple-shear launch may have rebuilt the list in the kernel since
+      // Hb was written; only the tilt changes there
+      s->st[r].Hb[1] = s->st[r].tilt_b;
+    }
+  }
   AQS_TRY(upload_state(s));
   std::vector<int64_t> rebuilds(s->R, 0);
   std::vector<int> kreb0(s->R);
@@ -612,6 +679,10 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
     }
     MinArgs a = min_args(s, f);
     a.warm_u = warm_u;
+    if (s->hist_launch) {
+      a.hist = s->d_hist;
+      a.hist_stride = s->hist_cap;
+    }
     const bool timing = g_timing.load() != 0;
     std::vector<RepState> before(s->st);
     if (timing) CUDA_TRY(cudaEventRecord(s->ev0, s->stream));
@@ -694,6 +765,7 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
     if (!next.empty() && std::count(flags.begin(), flags.end(), 1) > 0) AQS_TRY(rebuild(s, flags));
     todo.swap(next);
   }
+  s->hist_launch = false;
   if (!todo.empty()) return fail(AQS_ERR_TIMEOUT, "minimiser jobs did not finish");
   if (out) {
     out->stride = s->rec_cap;
@@ -834,6 +906,11 @@ aqs_status init_system(aqs_system* s, int dim, int R, const int64_t* n, const aq
     s->nmax = std::max(s->nmax, n[r]);
   }
   make_coef(s, pot);
+  {
+    std::array<double, 9> id{};
+    for (int a = 0; a < dim; a++) id[a * dim + a] = 1.0;
+    s->frame.assign(R, id);
+  }
   s->geom.assign(R, RepGeom{});
   s->st.assign(R, RepState{});
   s->mean_nb.assign(R, 0.0);
@@ -977,9 +1054,12 @@ aqs_status ensure_chains(aqs_system* s, int src, int P) {
 }
 
 // Copies replica `sr` of system a into replicas `drs` of system b, the copy k
-// sheared by shift[k]; velocities cleared.  Lists are not copied (rebuilt).
+// sheared by shift[k], or (maps non-null: host [ncopy][9]) mapped by the
+// upper-triangular maps[k] into the cell cells[k] (host [ncopy][9], 3 x 3
+// slots); velocities cleared.  Lists are not copied (rebuilt).
 aqs_status copy_replicas(aqs_system* a, int sr, aqs_system* b, const std::vector<int>& drs,
-                         const std::vector<double>& shift) {
+                         const std::vector<double>& shift, const double* maps = nullptr,
+                         const double* cells = nullptr) {
   RepCopy c;
   c.sx = a->x;
   c.sxb = a->xb;
@@ -1014,6 +1094,13 @@ aqs_status copy_replicas(aqs_system* a, int sr, aqs_system* b, const std::vector
   c.doff = b->d_i64;
   c.dnb_off = b->d_i64 + drs.size();
   c.shift = b->d_shift;
+  c.maps = nullptr;
+  if (maps) {
+    if (!b->d_maps) AQS_TRY(alloc_arr(b, &b->d_maps, (size_t)9 * b->R));
+    CUDA_TRY(cudaMemcpyAsync(b->d_maps, maps, sizeof(double) * 9 * drs.size(),
+                             cudaMemcpyHostToDevice, b->stream));
+    c.maps = b->d_maps;
+  }
   c.n = (int)a->n[sr];
   c.cap = 0;  // lists are rebuilt for the new owner layout
   c.ncopy = (int)drs.size();
@@ -1023,11 +1110,138 @@ aqs_status copy_replicas(aqs_system* a, int sr, aqs_system* b, const std::vector
   for (size_t k = 0; k < drs.size(); k++) {
     RepGeom& g = b->geom[drs[k]];
     std::memcpy(g.H, a->geom[sr].H, sizeof(g.H));
-    g.H[0 * D + 1] += shift[k] * g.H[1 * D + 1];
+    if (cells) {
+      for (int x = 0; x < D; x++)
+        for (int y = 0; y < D; y++) g.H[x * D + y] = cells[9 * k + x * 3 + y];
+    } else {
+      g.H[0 * D + 1] += shift[k] * g.H[1 * D + 1];
+    }
   }
   std::vector<uint8_t> flags(b->R, 0);
   for (int r : drs) flags[r] = 1;
   return rebuild(b, flags);
+}
+
+// ---- deformation histories (pure / pull-push shear, cyclic protocols) ----
+// The stored cell H is always upper triangular; the laboratory cell is Q H
+// with Q the replica's frame.  An increment F acts on the laboratory cell
+// (Eq. 1 with a general matrix): H_lab <- F H_lab, Q <- Gram-Schmidt frame of
+// the new H_lab, H <- Q^T H_lab, and stored positions move by the
+// upper-triangular M = Q_new^T F Q_old (Eq. 3 in the two frames).  For
+// simple shear Q stays the identity and M = F.
+
+// Columns q_c of the Gram-Schmidt frame of G (d x d, row-major): G = Q R,
+// R upper triangular with a positive diagonal.  Q is row-major d x d.
+void gs_frame(int D, const double* G, double* Q) {
+  double q[3][3] = {{0.0}};
+  double n0 = 0.0;
+  for (int a = 0; a < D; a++) n0 += G[a * D] * G[a * D];
+  n0 = std::sqrt(n0);
+  for (int a = 0; a < D; a++) q[0][a] = G[a * D] / n0;
+  double p = 0.0;
+  for (int a = 0; a < D; a++) p += q[0][a] * G[a * D + 1];
+  double n1 = 0.0;
+  for (int a = 0; a < D; a++) {
+    q[1][a] = G[a * D + 1] - p * q[0][a];
+    n1 += q[1][a] * q[1][a];
+  }
+  n1 = std::sqrt(n1);
+  for (int a = 0; a < D; a++) q[1][a] /= n1;
+  if (D == 3) {
+    q[2][0] = q[0][1] * q[1][2] - q[0][2] * q[1][1];
+    q[2][1] = q[0][2] * q[1][0] - q[0][0] * q[1][2];
+    q[2][2] = q[0][0] * q[1][1] - q[0][1] * q[1][0];
+  }
+  for (int a = 0; a < D; a++)
+    for (int c = 0; c < D; c++) Q[a * D + c] = q[c][a];
+}
+
+// One increment F from the frame Q and stored cell H (both updated); writes
+// the map M and the new cell in 3 x 3 slots.
+void hist_step(int D, double* Q, double* H, const double* F, double* M9, double* H9) {
+  double L[9], Ln[9], Qn[9], T[9];
+  for (int a = 0; a < D; a++)
+    for (int c = 0; c < D; c++) {
+      double v = 0.0;
+      for (int k = 0; k < D; k++) v += Q[a * D + k] * H[k * D + c];
+      L[a * D + c] = v;
+    }
+  for (int a = 0; a < D; a++)
+    for (int c = 0; c < D; c++) {
+      double v = 0.0;
+      for (int k = 0; k < D; k++) v += F[a * D + k] * L[k * D + c];
+      Ln[a * D + c] = v;
+    }
+  gs_frame(D, Ln, Qn);
+  for (int a = 0; a < D; a++)  // T = F Q_old
+    for (int c = 0; c < D; c++) {
+      double v = 0.0;
+      for (int k = 0; k < D; k++) v += F[a * D + k] * Q[k * D + c];
+      T[a * D + c] = v;
+    }
+  for (int k = 0; k < 9; k++) M9[k] = H9[k] = 0.0;
+  for (int a = 0; a < D; a++)
+    for (int c = a; c < D; c++) {
+      double m = 0.0, h = 0.0;
+      for (int k = 0; k < D; k++) {
+        m += Qn[k * D + a] * T[k * D + c];
+        h += Qn[k * D + a] * Ln[k * D + c];
+      }
+      M9[a * 3 + c] = m;
+      H9[a * 3 + c] = h;
+    }
+  for (int a = 0; a < D; a++)
+    for (int c = 0; c < D; c++) H[a * D + c] = H9[a * 3 + c];
+  std::memcpy(Q, Qn, sizeof(double) * D * D);
+}
+
+// A cell a history reaches must keep the minimum-image rule and (3D) its
+// tilt in xy only.
+aqs_status check_hist_cell(aqs_system* s, const double* H) {
+  const int D = s->dim;
+  if (D == 3 && (std::fabs(H[2]) > 0.0 || std::fabs(H[5]) > 0.0))
+    return fail(AQS_ERR_UNSUPPORTED, "3D deformation histories must keep the cell tilted in xy only");
+  if (!(H[0] > 0.0) || !(H[D + 1] > 0.0) || (D == 3 && !(H[8] > 0.0)))
+    return fail(AQS_ERR_INVALID_ARG, "deformation history inverts the cell");
+  double w[3];
+  cell_widths(D, H, w);
+  for (int c = 0; c < D; c++)
+    if (!(s->rlist * 3.0 <= w[c]))
+      return fail(AQS_ERR_BOX_TOO_SMALL, "deformation history: width %.4g < 3 (rc+skin) = %.4g",
+                  w[c], 3.0 * s->rlist);
+  return AQS_OK;
+}
+
+// Job table of one replica for n increments F[0..n) (d x d each) from (Q, H),
+// both advanced; with first_noaffine the job's step 0 has no increment (row
+// left as the identity map into the current cell).  Optionally returns the
+// product of the maps (3 x 3 slots).
+aqs_status hist_table(aqs_system* s, double* Q, double* H, const double* F, int64_t n,
+                      bool first_noaffine, std::vector<double>& table, double* Mprod = nullptr) {
+  const int D = s->dim;
+  const int64_t rows = n + (first_noaffine ? 1 : 0);
+  table.assign((size_t)rows * kHistFields, 0.0);
+  double P[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  int64_t row = 0;
+  if (first_noaffine) {
+    for (int a = 0; a < 3; a++) table[a * 3 + a] = 1.0;
+    for (int a = 0; a < D; a++)
+      for (int c = 0; c < D; c++) table[9 + a * 3 + c] = H[a * D + c];
+    row = 1;
+  }
+  for (int64_t k = 0; k < n; k++, row++) {
+    double* r = table.data() + row * kHistFields;
+    hist_step(D, Q, H, F + (size_t)k * D * D, r, r + 9);
+    if (D == 2) r[8] = 1.0;  // unused z slot of the map: identity
+    AQS_TRY(check_hist_cell(s, H));
+    double Pn[9] = {0};
+    for (int a = 0; a < 3; a++)
+      for (int c = 0; c < 3; c++)
+        for (int k2 = 0; k2 < 3; k2++) Pn[a * 3 + c] += r[a * 3 + k2] * P[k2 * 3 + c];
+    std::memcpy(P, Pn, sizeof(P));
+  }
+  if (Mprod) std::memcpy(Mprod, P, sizeof(P));
+  return AQS_OK;
 }
 
 aqs_status gather_user(aqs_system* s, int r, double* dst) {
@@ -1205,6 +1419,75 @@ aqs_status aqs_run_sequential(aqs_system* s, const aqs_fire_params* f, double dg
   return AQS_OK;
 }
 
+aqs_status aqs_deform(aqs_system* s, const double* F) {
+  if (!s || !F) return fail(AQS_ERR_INVALID_ARG, "null argument");
+  const int D = s->dim;
+  std::vector<double> maps((size_t)9 * s->R), cells((size_t)9 * s->R);
+  std::vector<std::array<double, 9>> fr(s->frame);
+  std::vector<uint8_t> flags(s->R, 1);
+  for (int r = 0; r < s->R; r++) {
+    for (int k = 0; k < D * D; k++)
+      if (!std::isfinite(F[(size_t)r * D * D + k])) return fail(AQS_ERR_INVALID_ARG, "non-finite F");
+    double H[9];
+    std::memcpy(H, s->geom[r].H, sizeof(H));
+    hist_step(D, fr[r].data(), H, F + (size_t)r * D * D, &maps[9 * r], &cells[9 * r]);
+    if (D == 2) maps[9 * r + 8] = 1.0;
+    AQS_TRY(check_hist_cell(s, H));  // nothing applied yet
+  }
+  if (!s->d_maps) AQS_TRY(alloc_arr(s, &s->d_maps, (size_t)9 * s->R));
+  CUDA_TRY(cudaMemcpyAsync(s->d_maps, maps.data(), sizeof(double) * maps.size(),
+                           cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(cudaMemcpyAsync(s->d_flag, flags.data(), s->R, cudaMemcpyHostToDevice, s->stream));
+  CUDA_TRY(launch_deform(D, s->x, s->xb, s->d_rep_of, s->d_flag, s->d_maps, s->ntot, s->stream));
+  for (int r = 0; r < s->R; r++) {
+    for (int a = 0; a < D; a++)
+      for (int c = 0; c < D; c++) s->geom[r].H[a * D + c] = cells[9 * r + a * 3 + c];
+    s->frame[r] = fr[r];
+  }
+  sync_tilt_to_state(s);
+  // the lists are rebuilt in the new cell (a stretch changes pair distances
+  // without changing the tilt the simple-shear skin test watches)
+  return rebuild(s, flags);
+}
+
+aqs_status aqs_run_history(aqs_system* s, const aqs_fire_params* f, const double* F,
+                           int64_t n_steps, double* energy, double* tau, int64_t* fire_iters,
+                           double* nonaffine_out) {
+  if (!s || !f || n_steps < 0 || (n_steps > 0 && !F)) return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  if (n_steps == 0) return AQS_OK;
+  const int D = s->dim;
+  for (int64_t k = 0; k < n_steps * D * D; k++)
+    if (!std::isfinite(F[k])) return fail(AQS_ERR_INVALID_ARG, "non-finite F");
+  std::vector<Job> jobs(s->R);
+  std::vector<std::array<double, 9>> fr(s->frame);
+  for (int r = 0; r < s->R; r++) {
+    double H[9];
+    std::memcpy(H, s->geom[r].H, sizeof(H));
+    AQS_TRY(hist_table(s, fr[r].data(), H, F, n_steps, false, jobs[r].table));
+    jobs[r].nsteps = n_steps;
+  }
+  JobOut out;
+  AQS_TRY(run_jobs(s, f, jobs, &out));
+  for (int r = 0; r < s->R; r++) s->frame[r] = fr[r];
+  AQS_TRY(rebuild_all(s));  // lists at the final cell for later simple-shear calls
+  for (int64_t k = 0; k < n_steps; k++)
+    for (int r = 0; r < s->R; r++) {
+      const double* rec = &out.rec[((size_t)r * out.stride + k) * kRecFields];
+      size_t i = (size_t)k * s->R + r;
+      if (energy) energy[i] = rec[0];
+      if (tau) tau[i] = rec[1];
+      if (fire_iters) fire_iters[i] = (int64_t)rec[3];
+      if (nonaffine_out) nonaffine_out[i] = rec[2];
+    }
+  return AQS_OK;
+}
+
+aqs_status aqs_get_frame(const aqs_system* s, int r, double* Q) {
+  if (!s || !Q || r < 0 || r >= s->R) return fail(AQS_ERR_INVALID_ARG, "bad argument");
+  std::memcpy(Q, s->frame[r].data(), sizeof(double) * s->dim * s->dim);
+  return AQS_OK;
+}
+
 aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
                              const aqs_parallel_params* p, aqs_parallel_result* out) {
   if (!s || !f || !p || !out) return fail(AQS_ERR_INVALID_ARG, "null argument");
@@ -1212,6 +1495,10 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
   if (p->K < 1 || p->P < 1 || p->n_steps < 0 || !std::isfinite(p->dgamma))
     return fail(AQS_ERR_INVALID_ARG, "bad parallel parameters");
   if (p->warm_start) return fail(AQS_ERR_UNSUPPORTED, "warm start is not available");
+  const double* Fh = p->F_steps;  // deformation history of this call (nullable)
+  if (Fh)
+    for (int64_t k = 0; k < p->n_steps * s->dim * s->dim; k++)
+      if (!std::isfinite(Fh[k])) return fail(AQS_ERR_INVALID_ARG, "non-finite F_steps");
   const double eq_tol = p->eq_tol > 0.0 ? p->eq_tol : 1e-6;
   const double ev_thr = p->event_threshold > 0.0 ? p->event_threshold : 1e-2;
   const int P = p->P, D = s->dim;
@@ -1246,12 +1533,39 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
       drs[i] = i;
       shift[i] = (double)i * K * p->dgamma;
     }
-    AQS_TRY(copy_replicas(s, src, c, drs, shift));
+    std::vector<Job> jobs(P);
+    std::vector<std::array<double, 9>> chain_frame(P_eff);
+    if (Fh) {
+      // level I under a history: chain i starts after the i K increments
+      // that follow the current step, applied one after the other (the
+      // sequence chain i-1 applies on its way), so that chain i starts in
+      // exactly the cell where chain i-1 ends; its job table continues the
+      // sequence with its own K_i increments
+      const int DD = D * D;
+      std::vector<double> maps((size_t)9 * P_eff), cells((size_t)9 * P_eff);
+      for (int i = 0; i < P_eff; i++) {
+        std::array<double, 9> Q = s->frame[src];
+        double H[9];
+        std::memcpy(H, s->geom[src].H, sizeof(H));
+        std::vector<double> lvl1;
+        AQS_TRY(hist_table(s, Q.data(), H, Fh + (size_t)n_cur * DD, (int64_t)i * K, false, lvl1,
+                           &maps[9 * i]));
+        for (int k = 0; k < 9; k++) cells[9 * i + k] = 0.0;
+        for (int a = 0; a < D; a++)
+          for (int cc = 0; cc < D; cc++) cells[9 * i + a * 3 + cc] = H[a * D + cc];
+        c->frame[i] = Q;
+        AQS_TRY(hist_table(s, Q.data(), H, Fh + (size_t)(n_cur + (int64_t)i * K) * DD, Ki[i],
+                           true, jobs[i].table));
+        chain_frame[i] = Q;
+      }
+      AQS_TRY(copy_replicas(s, src, c, drs, shift, maps.data(), cells.data()));
+    } else {
+      AQS_TRY(copy_replicas(s, src, c, drs, shift));
+    }
     // level II (Eq. 19): chain i runs F once (its outgoing configuration,
     // kept as a caller-order snapshot for i >= 1) and then K_i fine AQS
     // steps, all inside persistent launches; chains never wait for each other
     // between fine steps
-    std::vector<Job> jobs(P);
     for (int i = 0; i < P_eff; i++) {
       jobs[i].nsteps = 1 + Ki[i];
       jobs[i].dgamma = p->dgamma;
@@ -1373,6 +1687,7 @@ aqs_status aqs_parallel_step(aqs_system* s, int src, const aqs_fire_params* f,
       }
     // r_star <- r_q: the end of chain `last`
     AQS_TRY(copy_replicas(c, last, s, std::vector<int>{src}, std::vector<double>{0.0}));
+    if (Fh) s->frame[src] = chain_frame[last];
     n_cur += q;
     out->accepted_steps += q;
     out->iterations++;
@@ -1444,6 +1759,8 @@ aqs_status aqs_set_box(aqs_system* s, int r, const double* H) {
   if (!s || !H || r < 0 || r >= s->R) return fail(AQS_ERR_INVALID_ARG, "bad argument");
   AQS_TRY(check_box(s, r, H));
   std::memcpy(s->geom[r].H, H, sizeof(double) * s->dim * s->dim);
+  for (int k = 0; k < 9; k++) s->frame[r][k] = 0.0;
+  for (int a = 0; a < s->dim; a++) s->frame[r][a * s->dim + a] = 1.0;
   std::vector<uint8_t> flags(s->R, 0);
   flags[r] = 1;
   return rebuild(s, flags);
