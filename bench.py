@@ -572,6 +572,129 @@ def run_glass3d(args):
                       "cluster_size": b.cluster_size(0), "staging": b.staging(0)}})
 
 
+def run_sweep(args):
+    """The paper's experiment (Sec. 4) on the GPU: its S/L glass model (N =
+    400, density 1), simple shear dgamma = 1/200 for 200 steps (gamma = 1),
+    for every glass j (seeds 0..n-1, FP64 GPU quench of the seeded start) the
+    run time C_S of sequential AQS and C_(P,K) of Algorithm 1 for P in
+    {4, 8, 16, 32} and K in {1, 2, 6, 10, 14, 16}; speed-up S_j = C_S / C_(P,K),
+    and its mean mu and standard deviation sigma over the glasses (the paper's
+    definitions).  Every run's final configuration is checked to equal the
+    sequential one (1e-6 sigma), as the paper reports for its runs.  Mixed
+    precision, device time.  value = mu at (P, K) = (32, 10)."""
+    import torch
+    from paper_2507_20802_gb300 import aqs as A, synthetic as syn
+    torch.cuda.set_device(0)
+    n, dg, steps = 400, 1.0 / 200.0, 200
+    Ps, Ks = args.sweep_P, args.sweep_K
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        e1.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    def mi(a, b, H):
+        d = a - b
+        for c in (1, 0):
+            d -= np.round(d[:, c] / H[c, c])[:, None] * H[:, c][None, :]
+        d -= d.mean(axis=0)
+        return float(np.sqrt((d * d).sum(1)).max())
+
+    S = {(P, K): [] for P in Ps for K in Ks}
+    seq_s, all_equal, rej = [], True, {}
+    l0 = A.aqs_launch_count()
+    with Clocks(0) as clk:
+        for seed in range(args.sweep_seeds):
+            x, t, H = syn.random_glass_start(n, 2, seed, fraction_a=syn.SL_FRACTION_S,
+                                             density=syn.SL_DENSITY)
+            g = A.System(x, t, H[None], [n], syn.SL_SIGMA, syn.SL_EPS, syn.RC_FACTOR,
+                         precision=A.AQS_FP64)
+            assert g.minimize(A.fire_params(max_iter=2_000_000))[0]["status"] == 0
+            xq, Hq = g.positions(), g.box()
+            g.close()
+
+            def mk():
+                return A.System(xq, t, Hq[None], [n], syn.SL_SIGMA, syn.SL_EPS, syn.RC_FACTOR,
+                                precision=A.AQS_MIXED)
+            s0 = mk()
+            s0.run_sequential(dg, 2)  # warm-up of this glass's launch path
+            s0.close()
+            s0 = mk()
+            _, cs = timed(lambda: s0.run_sequential(dg, steps))
+            x_seq, H_seq = s0.positions(), s0.box()
+            s0.close()
+            seq_s.append(cs)
+            for P in Ps:
+                for K in Ks:
+                    sp = mk()
+                    r, cp = timed(lambda: sp.parallel_step(dg, K, P, steps))
+                    all_equal = all_equal and mi(sp.positions(), x_seq, H_seq) < 1e-6
+                    rej[(P, K)] = rej.get((P, K), 0) + int(r["rejections"])
+                    sp.close()
+                    S[(P, K)].append(cs / cp)
+    table = []
+    for P in Ps:
+        for K in Ks:
+            v = np.array(S[(P, K)])
+            table.append({"P": P, "K": K, "mu": float(v.mean()), "sigma": float(v.std()),
+                          "S": [float(a) for a in v], "rejections": rej[(P, K)]})
+    head = next((r for r in table if r["P"] == 32 and r["K"] == 10), table[-1])
+    config = {"workload": "the paper's S/L glass (N=400, density 1), dgamma=1/200, 200 steps, "
+                          "%d glasses (seeds 0..%d, FP64 GPU quench), mixed precision, "
+                          "P in %s, K in %s" % (args.sweep_seeds, args.sweep_seeds - 1, Ps, Ks),
+              "l2": "working set on chip; not flushed"}
+    _line("Algorithm 1 speed-up mu over sequential AQS (the paper's mu, P=%d, K=%d)"
+          % (head["P"], head["K"]), head["mu"], "x", args, 1e3 * float(np.mean(seq_s)), config,
+          {"gpu_launches": A.aqs_launch_count() - l0, "clocks": clk.summary(),
+           "sigma": head["sigma"], "all_final_configurations_equal": all_equal,
+           "sequential_s": [float(a) for a in seq_s], "table": table,
+           "paper": "mu 2.02 (P=4, K=1) to 6.33 (P=32, K=10), CPU threads, hardware not stated"})
+
+
+def run_tune_table(args):
+    """The launch-configuration table of the benchmark's level-II chains: the
+    N = 4096 glass (FP64 GPU quench of seed 0) in 16 replicas at the level-I
+    strains i K dgamma, minimised and sheared one fine step, then the
+    autotuner's time per FIRE iteration for every cluster size (and the
+    staging modes at the best one), with one thread per atom and with the
+    split force phase allowed; also for a single replica (the sequential
+    AQS shape).  Prints one line."""
+    import torch
+    from paper_2507_20802_gb300 import aqs as A, synthetic as syn
+    torch.cuda.set_device(0)
+    x, t, H = syn.random_glass_start(N_ATOMS, 2, seed=0)
+    g = A.System(x, t, H[None], [N_ATOMS], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
+                 precision=A.AQS_FP64)
+    assert g.minimize(A.fire_params(max_iter=2_000_000))[0]["status"] == 0
+    xq, Hq = g.positions(), g.box()
+    g.close()
+    rows = []
+    for R in (P_CHAINS, 1):
+        s = A.System(np.tile(xq, (R, 1)), np.tile(t, R), np.tile(Hq[None], (R, 1, 1)),
+                     [N_ATOMS] * R, syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
+                     precision=A.AQS_MIXED)
+        s.shear(np.arange(R) * K_FINE * DGAMMA)
+        s.minimize()
+        s.shear(np.full(R, DGAMMA))
+        for tpa in (1, 2, 0):
+            s.set_threads_per_atom(tpa)
+            C, mode, msC, msM = s.autotune(iters=args.tune_iters)
+            rows.append({"replicas": R, "threads_per_atom": {1: "1", 2: "2", 0: "tuned"}[tpa],
+                         "chosen_threads_per_atom": s.threads_per_atom(), "best_C": C,
+                         "staging": mode,
+                         "us_per_iter_by_C": {c: round(v * 1e3, 2) for c, v in msC.items()},
+                         "us_per_iter_by_staging": {m: round(v * 1e3, 2)
+                                                    for m, v in msM.items()}})
+        s.close()
+    print(json.dumps({"metric": "minimiser time per FIRE iteration by launch configuration",
+                      "unit": "us", "config": CONFIG, "iters_per_candidate": args.tune_iters,
+                      "rows": rows}), flush=True)
+
+
 def quench_3d(A, syn, n, seed, max_iter):
     """The 3D glass of the cfg3 workload: seeded random start, mixed-precision
     GPU FIRE quench (status and iterations returned; not converged when the
@@ -718,7 +841,12 @@ def main():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--baseline-steps", type=int, default=20)
     ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d", "cfg3", "warm",
-                                           "oracle-threads"], default="cfg1")
+                                           "oracle-threads", "sweep", "tune-table"],
+                    default="cfg1")
+    ap.add_argument("--tune-iters", type=int, default=500)
+    ap.add_argument("--sweep-seeds", type=int, default=4)
+    ap.add_argument("--sweep-P", type=int, nargs="+", default=[4, 8, 16, 32])
+    ap.add_argument("--sweep-K", type=int, nargs="+", default=[1, 2, 6, 10, 14, 16])
     ap.add_argument("--no-force3d", action="store_true",
                     help="skip the 3D force-kernel bandwidth figure of the default line")
     ap.add_argument("--oracle-steps", type=int, default=60)
@@ -750,6 +878,10 @@ def main():
         return run_oracle_threads(args) or 0
     if args.workload == "cfg3":
         return run_cfg3(args) or 0
+    if args.workload == "sweep":
+        return run_sweep(args) or 0
+    if args.workload == "tune-table":
+        return run_tune_table(args) or 0
 
     import torch
     ws, rank, local = _dist()

@@ -380,14 +380,18 @@ aqs_status aqs_energy_forces_noalloc(int dim, int64_t n, const double* pos, cons
 
 /* Times `iters` FIRE iterations (convergence test disabled, so every candidate
  * does the same work from the same configuration) of the replicas with
- * mask[r] != 0 (NULL = all): first every feasible C in 1..16 (at most 4096 and
- * at least 32 atoms per CTA, at least one cluster resident) with automatic
- * staging, then every staging mode that fits at the fastest C.  Keeps the
- * fastest pair for those replicas (unless aqs_set_staging fixed the mode).
- * Outputs, each may be NULL: *best_cluster, *best_staging (-1 = automatic);
+ * mask[r] != 0 (NULL = all): every feasible C in 1..16 (at most 4096 and at
+ * least 32 atoms per CTA, at least one cluster resident), each with every
+ * staging mode that fits and with one and (where it fits) two threads per
+ * atom in the force phase (the staging mode sets a CTA's shared memory and so
+ * how many CTAs of different clusters share an SM, i.e. how many replicas'
+ * clusters are resident at once).  Keeps the fastest (C, staging, threads per
+ * atom), except what aqs_set_staging / aqs_set_threads_per_atom fixed;
+ * ms_per_iter[C] is the fastest candidate at C.
+ * Outputs, each may be NULL: *best_cluster, *best_staging;
  * ms_per_iter[17] (entry C: wall time per iteration in ms, -1 if C was not
  * feasible; entry 0 unused); ms_per_staging[4] (entry m: time per iteration
- * at the best C in mode m, -1 if not timed).  Positions, boxes and minimiser
+ * at the best C and threads per atom in mode m, -1 if not timed).  Positions, boxes and minimiser
  * state are restored afterwards, so tuning does not change the
  * configuration.  Errors as aqs_minimize, except that not converging is the
  * expected outcome. */
@@ -409,6 +413,14 @@ aqs_status aqs_set_autotune(aqs_system* sys, int64_t iters);
  * replica per launch.  Results agree within the precision's tolerance (the
  * FP64 re-reference points move).  Applies to the system and its chains. */
 aqs_status aqs_set_launch_budget(aqs_system* sys, int64_t iters);
+/* Threads per atom in the force phase of the minimiser ("atoms per warp"
+ * 32 / tpa): 1, or 2 (each atom's list split between two adjacent lanes that
+ * sum their partial forces in a fixed order; used where 2 x atoms-per-CTA
+ * threads fit a CTA, else 1), or 0 to let the autotuner choose (1 without
+ * it).  Applies to the system and its chains.  Results agree with tpa = 1
+ * within rounding (the force sums are added in another order). */
+aqs_status aqs_set_threads_per_atom(aqs_system* sys, int tpa);
+int aqs_threads_per_atom(const aqs_system* sys);
 /* Fixes the staging mode (0..3) of this system and its chains, or -1 for the
  * automatic choice.  AQS_ERR_INVALID_ARG outside -1..3. */
 aqs_status aqs_set_staging(aqs_system* sys, int mode);

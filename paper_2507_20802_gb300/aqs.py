@@ -139,6 +139,8 @@ _SIGS = {
                                         C.POINTER(C.c_double)]),
     "aqs_set_autotune": (C.c_int, [C.c_void_p, C.c_int64]),
     "aqs_set_launch_budget": (C.c_int, [C.c_void_p, C.c_int64]),
+    "aqs_set_threads_per_atom": (C.c_int, [C.c_void_p, C.c_int]),
+    "aqs_threads_per_atom": (C.c_int, [C.c_void_p]),
     "aqs_set_staging": (C.c_int, [C.c_void_p, C.c_int]),
     "aqs_staging": (C.c_int, [C.c_void_p, C.c_int]),
     "aqs_set_kernel_timing": (None, [C.c_int]),
@@ -561,6 +563,12 @@ class System:
 
     def set_launch_budget(self, iters):
         check(lib().aqs_set_launch_budget(self.h, C.c_int64(iters)))
+
+    def set_threads_per_atom(self, tpa):
+        check(lib().aqs_set_threads_per_atom(self.h, int(tpa)))
+
+    def threads_per_atom(self):
+        return lib().aqs_threads_per_atom(self.h)
 
     def set_staging(self, mode):
         check(lib().aqs_set_staging(self.h, int(mode)))

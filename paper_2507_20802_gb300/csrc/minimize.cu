@@ -51,11 +51,24 @@ int minimize_staging(int dim, int npc, int nrep, int nt, int cap, int want) {
   return choose_mem(dim, npc, nrep, nt, cap, want);
 }
 
+int minimize_tpa(int npc, int want) { return effective_tpa(npc, want); }
+
+bool minimize_launch_is_lean(int dim, int npc, int tpa) {
+  return effective_tpa(npc, tpa) > 1 || minimize_is_lean(dim, minimize_atoms_per_thread(dim, npc));
+}
+
 static cudaError_t dispatch(int dim, bool mixed, const MinArgs* a, int n_clusters, int C, int npc,
                             int nrep, int nt, int cap, cudaStream_t s, int* max_clusters,
-                            int staging) {
+                            int staging, int tpa) {
   int mem = choose_mem(dim, npc, nrep, nt, cap, staging);
   size_t smem = minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, mem);
+  if (effective_tpa(npc, tpa) == 2) {
+    if (dim == 2)
+      return mixed ? run_mem_2_mixed_t2(mem, a, n_clusters, C, npc, smem, s, max_clusters)
+                   : run_mem_2_fp64_t2(mem, a, n_clusters, C, npc, smem, s, max_clusters);
+    return mixed ? run_mem_3_mixed_t2(mem, a, n_clusters, C, npc, smem, s, max_clusters)
+                 : run_mem_3_fp64_t2(mem, a, n_clusters, C, npc, smem, s, max_clusters);
+  }
   if (dim == 2)
     return mixed ? run_mem_2_mixed(mem, a, n_clusters, C, npc, smem, s, max_clusters)
                  : run_mem_2_fp64(mem, a, n_clusters, C, npc, smem, s, max_clusters);
@@ -64,16 +77,16 @@ static cudaError_t dispatch(int dim, bool mixed, const MinArgs* a, int n_cluster
 }
 
 cudaError_t launch_minimize(int dim, bool mixed, MinArgs a, int n_clusters, int C, int npc,
-                            int nrep, int cap, cudaStream_t s, int staging) {
+                            int nrep, int cap, cudaStream_t s, int staging, int tpa) {
   a.npc_launch = npc;
   a.nrep_launch = nrep;
-  return dispatch(dim, mixed, &a, n_clusters, C, npc, nrep, a.nt, cap, s, nullptr, staging);
+  return dispatch(dim, mixed, &a, n_clusters, C, npc, nrep, a.nt, cap, s, nullptr, staging, tpa);
 }
 
 int minimize_max_active_clusters(int dim, bool mixed, int C, int npc, int nrep, int nt, int cap,
-                                 int staging) {
+                                 int staging, int tpa) {
   int m = 0;
-  if (dispatch(dim, mixed, nullptr, 1, C, npc, nrep, nt, cap, nullptr, &m, staging) !=
+  if (dispatch(dim, mixed, nullptr, 1, C, npc, nrep, nt, cap, nullptr, &m, staging, tpa) !=
       cudaSuccess) {
     cudaGetLastError();
     return 0;

@@ -70,8 +70,14 @@ size_t minimize_smem_bytes(int dim, int npc, int nrep, int nt, int cap, int mem)
 // staging mode used for this configuration: `want` if it fits in shared
 // memory (want in 0..3), else the automatic choice (2, then 1, then 0)
 int minimize_staging(int dim, int npc, int nrep, int nt, int cap, int want);
+// tpa: threads per atom of the force phase wanted (1, or 2 where npc * 2
+// threads fit in a CTA; see minimize_tpa)
 cudaError_t launch_minimize(int dim, bool mixed, MinArgs a, int n_clusters, int C, int npc,
-                            int nrep, int cap, cudaStream_t s, int staging = -1);
+                            int nrep, int cap, cudaStream_t s, int staging = -1, int tpa = 1);
+// threads per atom a launch with npc atoms per CTA uses when `want` is asked
+int minimize_tpa(int npc, int want);
+// the launch keeps per-atom state in MinArgs::lean32 / lean64
+bool minimize_launch_is_lean(int dim, int npc, int tpa);
 // atoms per thread of a launch with npc atoms per CTA (1, 2, 4 or 8; lean
 // launches use up to 1024 threads, the others up to 512)
 int minimize_atoms_per_thread(int dim, int npc);
@@ -80,6 +86,6 @@ int minimize_atoms_per_thread(int dim, int npc);
 constexpr bool minimize_is_lean(int dim, int apt) { return apt >= 4 || (dim == 3 && apt >= 2); }
 // clusters of C CTAs that can be resident at once for this configuration
 int minimize_max_active_clusters(int dim, bool mixed, int C, int npc, int nrep, int nt, int cap,
-                                 int staging = -1);
+                                 int staging = -1, int tpa = 1);
 
 }  // namespace aqs

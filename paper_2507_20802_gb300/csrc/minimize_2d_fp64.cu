@@ -7,7 +7,7 @@ namespace aqs {
 
 cudaError_t run_mem_2_fp64(int mem, const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
                          cudaStream_t s, int* max_clusters) {
-  return run_mem<2, false>(mem, a, n_clusters, C, npc, smem, s, max_clusters);
+  return run_mem<2, false, 1>(mem, a, n_clusters, C, npc, smem, s, max_clusters);
 }
 
 }  // namespace aqs

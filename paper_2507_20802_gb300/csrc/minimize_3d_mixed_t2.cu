@@ -1,0 +1,13 @@
+// minimize_3d_mixed_t2.cu -- instantiation of the persistent minimiser for
+// dimension 3, mixed precision, with the split force phase (two threads per
+// atom); its own unit so that the variants compile in parallel.
+#include "minimize_launch.cuh"
+
+namespace aqs {
+
+cudaError_t run_mem_3_mixed_t2(int mem, const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
+                  cudaStream_t s, int* max_clusters) {
+  return run_mem<3, true, 2>(mem, a, n_clusters, C, npc, smem, s, max_clusters);
+}
+
+}  // namespace aqs

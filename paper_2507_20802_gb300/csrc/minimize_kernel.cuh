@@ -201,8 +201,15 @@ constexpr double kBigV2 = 1e30;
 // gathers; 2 = list staged and, every iteration, the positions of all CTAs
 // that own neighbours copied into the local shared memory, so the force loop
 // reads local shared memory only.
-template <int D, bool MIXED, int APT, int MEM>
-__global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_minimize(MinArgs A) {
+// TPA: threads per atom in the force phase.  With TPA > 1 (one atom per
+// thread group of TPA adjacent lanes, APT = 1, per-atom state in global
+// memory) each lane of the group visits every TPA-th list entry and the group
+// sums its partial forces by shuffles in a fixed order; the other phases keep
+// one thread per atom.  It halves the serial pair chain of each thread and
+// doubles the warps that hide its latency.
+template <int D, bool MIXED, int APT, int MEM, int TPA>
+__global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 : 512, 1)
+    k_minimize(MinArgs A) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -307,7 +314,8 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
   // registers would spill, so it lives in global memory (L2) and only the
   // atom being processed is in registers: FP32 reference position, displacement, velocity, reference
   // force and the force used by the update, and the FP64 force.
-  constexpr bool LEAN = minimize_is_lean(D, APT);
+  constexpr bool LEAN = minimize_is_lean(D, APT) || TPA > 1;
+  static_assert(TPA == 1 || APT == 1, "split force phase runs one atom per thread group");
   // pair-loop unrolling: lean launches keep more list and record loads in
   // flight per thread (they stream the lists from HBM)
   constexpr int kPairUnroll = LEAN ? 8 : 4;
@@ -714,17 +722,44 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
           Fu[k][c] = 0.0f;
         }
       }
-      int li = tid + k * nthr;
+      // force-phase atom of this thread: li (TPA > 1: shared by TPA lanes, this
+      // lane's list entries are those with j = h mod TPA)
+      const int li = TPA > 1 ? tid / TPA : tid + k * nthr;
+      const int h = TPA > 1 ? (tid & (TPA - 1)) : 0;
       if (li >= cnt) continue;
       int64_t gi = base + li;
       const uint32_t* row = A.nb + g.nb_off + lo + li;
       const int nn = A.nnb[gi];
-      const int ti = ty[k];
+      const int ti = TPA > 1 ? A.type[gi] : ty[k];
+      // per-atom state of this atom (written by the group's first lane)
+      auto FDa = [&](int c) -> double& {
+        if constexpr (TPA > 1) return l64[c * N + gi];
+        else return FD(k, c);
+      };
+      auto FRa = [&](int c) -> float& {
+        if constexpr (TPA > 1) return l32[(3 * 3 + c) * N + gi];
+        else return FR(k, c);
+      };
+      auto FUa = [&](int c) -> float& {
+        if constexpr (TPA > 1) return l32[(4 * 3 + c) * N + gi];
+        else return FU(k, c);
+      };
+      auto Qa = [&](int c) -> float& {
+        if constexpr (TPA > 1) return l32[(0 * 3 + c) * N + gi];
+        else return Q(k, c);
+      };
+      auto Va = [&](int c) -> float& {
+        if constexpr (TPA > 1) return l32[(2 * 3 + c) * N + gi];
+        else return V(k, c);
+      };
+      // lanes of this atom's group (a subset of the warp: the groups of a
+      // warp need not all have an atom)
+      const unsigned gmask = TPA > 1 ? (((1u << TPA) - 1u) << (lane & ~(TPA - 1))) : 0xffffffffu;
       if (mode == kModeEval64) {
         double qi[3], e = 0.0, w = 0.0, Fk[3] = {0.0, 0.0, 0.0};
         load_pub64<D>(&mine[li], qi);
 #pragma unroll 4
-        for (int j = 0; j < nn; j++) {
+        for (int j = h; j < nn; j += TPA) {
           uint32_t ent = LSM ? lst[j * lstride + li] : __ldcs(row + (int64_t)j * n);
           double qj[3], d[3];
           load_pub64<D>(nbrec(ent), qj);
@@ -733,39 +768,47 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
           for (int c = 0; c < D; c++) d[c] = (qj[c] - qi[c]) + of[c];
           pair64<D>(coef[ti * A.nt + nb_type(ent)], d, Fk, want_e, e, w);
         }
+        if constexpr (TPA > 1) {
 #pragma unroll
-        for (int c = 0; c < D; c++) FD(k, c) = Fk[c];
+          for (int o = 1; o < TPA; o <<= 1)
+#pragma unroll
+            for (int c = 0; c < D; c++) Fk[c] += __shfl_xor_sync(gmask, Fk[c], o);
+        }
         r[6] += e;
         r[7] += w;
-        double f2 = 0.0, pv = 0.0, v2 = 0.0, u2 = 0.0;
+        if (h == 0) {
 #pragma unroll
-        for (int c = 0; c < D; c++) {
-          double vc = (MIXED && !v64) ? (double)V(k, c) : A.v[c * N + gi];
-          f2 = fma(Fk[c], Fk[c], f2);
-          pv = fma(Fk[c], vc, pv);
-          v2 = fma(vc, vc, v2);
-          double u = A.x[c * N + gi] - A.xb[c * N + gi];
-          u2 = fma(u, u, u2);
-        }
-        if (MIXED) {
+          for (int c = 0; c < D; c++) FDa(c) = Fk[c];
+          double f2 = 0.0, pv = 0.0, v2 = 0.0, u2 = 0.0;
 #pragma unroll
           for (int c = 0; c < D; c++) {
-            FR(k, c) = (float)Fk[c];
-            FU(k, c) = (float)Fk[c];
-            Q(k, c) = (float)qi[c];
+            double vc = (MIXED && !v64) ? (double)Va(c) : A.v[c * N + gi];
+            f2 = fma(Fk[c], Fk[c], f2);
+            pv = fma(Fk[c], vc, pv);
+            v2 = fma(vc, vc, v2);
+            double u = A.x[c * N + gi] - A.xb[c * N + gi];
+            u2 = fma(u, u, u2);
           }
+          if (MIXED) {
+#pragma unroll
+            for (int c = 0; c < D; c++) {
+              FRa(c) = (float)Fk[c];
+              FUa(c) = (float)Fk[c];
+              Qa(c) = (float)qi[c];
+            }
+          }
+          r[0] = nmax(r[0], f2);
+          r[1] += pv;
+          r[2] += f2;
+          r[3] += v2;
+          r[5] = nmax(r[5], u2);
         }
-        r[0] = nmax(r[0], f2);
-        r[1] += pv;
-        r[2] += f2;
-        r[3] += v2;
-        r[5] = nmax(r[5], u2);
       } else {
         float qi[3], di[3], f[3] = {0.f, 0.f, 0.f};
         load_pub32<D>(&mine[li], qi, di);
         auto pair_loop = [&](auto coef_of) {
 #pragma unroll kPairUnroll
-          for (int j = 0; j < nn; j++) {
+          for (int j = h; j < nn; j += TPA) {
             uint32_t ent = LSM ? lst[j * lstride + li] : __ldcs(row + (int64_t)j * n);
             float qj[3], dj[3], d0[3], e[3];
             load_pub32<D>(nbrec(ent), qj, dj);
@@ -786,23 +829,31 @@ __global__ void __launch_bounds__(minimize_is_lean(D, APT) ? 1024 : 512, 1) k_mi
         } else {
           pair_loop([&](int tj) { return coef32(coef[ti * A.nt + tj]); });
         }
-        float f2 = 0.f, v2 = 0.f, dd = 0.f;
-        double pv = 0.0;  // FP32 products are exact in FP64
+        if constexpr (TPA > 1) {
 #pragma unroll
-        for (int c = 0; c < D; c++) {
-          const float fu = FR(k, c) + f[c];
-          const float vk = V(k, c);
-          FU(k, c) = fu;
-          f2 = fmaf(fu, fu, f2);
-          pv = fma((double)fu, (double)vk, pv);
-          v2 = fmaf(vk, vk, v2);
-          dd = fmaf(di[c], di[c], dd);  // the published displacement
+          for (int o = 1; o < TPA; o <<= 1)
+#pragma unroll
+            for (int c = 0; c < D; c++) f[c] += __shfl_xor_sync(gmask, f[c], o);
         }
-        rf[0] = nmaxf(rf[0], f2);
-        rp += pv;
-        rf[2] += f2;
-        rf[3] += v2;
-        rf[4] = nmaxf(rf[4], dd);
+        if (h == 0) {
+          float f2 = 0.f, v2 = 0.f, dd = 0.f;
+          double pv = 0.0;  // FP32 products are exact in FP64
+#pragma unroll
+          for (int c = 0; c < D; c++) {
+            const float fu = FRa(c) + f[c];
+            const float vk = Va(c);
+            FUa(c) = fu;
+            f2 = fmaf(fu, fu, f2);
+            pv = fma((double)fu, (double)vk, pv);
+            v2 = fmaf(vk, vk, v2);
+            dd = fmaf(di[c], di[c], dd);  // the published displacement
+          }
+          rf[0] = nmaxf(rf[0], f2);
+          rp += pv;
+          rf[2] += f2;
+          rf[3] += v2;
+          rf[4] = nmaxf(rf[4], dd);
+        }
       }
     }
 

@@ -27,7 +27,16 @@ inline int choose_mem(int dim, int npc, int nrep, int nt, int cap, int want = -1
   return 0;
 }
 
-inline void choose_apt(int dim, int npc, int* apt, int* threads) {
+// threads per atom of the force phase a launch can use: `want` (2) when
+// npc * want threads fit in one CTA, else 1
+inline int effective_tpa(int npc, int want) { return (want == 2 && npc * 2 <= 1024) ? 2 : 1; }
+
+inline void choose_apt(int dim, int npc, int* apt, int* threads, int tpa = 1) {
+  if (tpa > 1) {
+    *apt = 1;
+    *threads = ((npc * tpa + 31) / 32) * 32;
+    return;
+  }
   *apt = npc <= 512 ? 1 : (npc <= 1024 ? 2 : (npc <= 2048 ? 4 : 8));
   // lean launches hold little per-thread state and may use up to 1024
   // threads: halve the atoms per thread where the result is still lean
@@ -36,10 +45,10 @@ inline void choose_apt(int dim, int npc, int* apt, int* threads) {
   *threads = ((t + 31) / 32) * 32;
 }
 
-template <int D, bool MIXED, int APT, int MEM>
+template <int D, bool MIXED, int APT, int MEM, int TPA>
 cudaError_t run_t(const MinArgs* a, int n_clusters, int C, int threads, size_t smem,
                          cudaStream_t s, int* max_clusters) {
-  auto kern = k_minimize<D, MIXED, APT, MEM>;
+  auto kern = k_minimize<D, MIXED, APT, MEM, TPA>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (C > 8) {
@@ -63,28 +72,32 @@ cudaError_t run_t(const MinArgs* a, int n_clusters, int C, int threads, size_t s
   return cudaLaunchKernelEx(&cfg, kern, *a);
 }
 
-template <int D, bool MIXED, int MEM>
+template <int D, bool MIXED, int MEM, int TPA>
 cudaError_t run_apt(const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
                            cudaStream_t s, int* max_clusters) {
   int apt, threads;
-  choose_apt(D, npc, &apt, &threads);
-  if (threads > (minimize_is_lean(D, apt) ? 1024 : 512)) return cudaErrorInvalidValue;
-  switch (apt) {
-    case 1: return run_t<D, MIXED, 1, MEM>(a, n_clusters, C, threads, smem, s, max_clusters);
-    case 2: return run_t<D, MIXED, 2, MEM>(a, n_clusters, C, threads, smem, s, max_clusters);
-    case 4: return run_t<D, MIXED, 4, MEM>(a, n_clusters, C, threads, smem, s, max_clusters);
-    default: return run_t<D, MIXED, 8, MEM>(a, n_clusters, C, threads, smem, s, max_clusters);
+  choose_apt(D, npc, &apt, &threads, TPA);
+  if (threads > ((minimize_is_lean(D, apt) || TPA > 1) ? 1024 : 512)) return cudaErrorInvalidValue;
+  if constexpr (TPA > 1) {
+    return run_t<D, MIXED, 1, MEM, TPA>(a, n_clusters, C, threads, smem, s, max_clusters);
+  } else {
+    switch (apt) {
+      case 1: return run_t<D, MIXED, 1, MEM, 1>(a, n_clusters, C, threads, smem, s, max_clusters);
+      case 2: return run_t<D, MIXED, 2, MEM, 1>(a, n_clusters, C, threads, smem, s, max_clusters);
+      case 4: return run_t<D, MIXED, 4, MEM, 1>(a, n_clusters, C, threads, smem, s, max_clusters);
+      default: return run_t<D, MIXED, 8, MEM, 1>(a, n_clusters, C, threads, smem, s, max_clusters);
+    }
   }
 }
 
-template <int D, bool MIXED>
+template <int D, bool MIXED, int TPA>
 cudaError_t run_mem(int mem, const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
                            cudaStream_t s, int* max_clusters) {
   switch (mem) {
-    case 3: return run_apt<D, MIXED, 3>(a, n_clusters, C, npc, smem, s, max_clusters);
-    case 2: return run_apt<D, MIXED, 2>(a, n_clusters, C, npc, smem, s, max_clusters);
-    case 1: return run_apt<D, MIXED, 1>(a, n_clusters, C, npc, smem, s, max_clusters);
-    default: return run_apt<D, MIXED, 0>(a, n_clusters, C, npc, smem, s, max_clusters);
+    case 3: return run_apt<D, MIXED, 3, TPA>(a, n_clusters, C, npc, smem, s, max_clusters);
+    case 2: return run_apt<D, MIXED, 2, TPA>(a, n_clusters, C, npc, smem, s, max_clusters);
+    case 1: return run_apt<D, MIXED, 1, TPA>(a, n_clusters, C, npc, smem, s, max_clusters);
+    default: return run_apt<D, MIXED, 0, TPA>(a, n_clusters, C, npc, smem, s, max_clusters);
   }
 }
 
@@ -97,5 +110,14 @@ cudaError_t run_mem_3_fp64(int mem, const MinArgs* a, int n_clusters, int C, int
                            cudaStream_t s, int* max_clusters);
 cudaError_t run_mem_3_mixed(int mem, const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
                             cudaStream_t s, int* max_clusters);
+// the split force phase (two threads per atom), one unit each
+cudaError_t run_mem_2_fp64_t2(int mem, const MinArgs* a, int n_clusters, int C, int npc,
+                              size_t smem, cudaStream_t s, int* max_clusters);
+cudaError_t run_mem_2_mixed_t2(int mem, const MinArgs* a, int n_clusters, int C, int npc,
+                               size_t smem, cudaStream_t s, int* max_clusters);
+cudaError_t run_mem_3_fp64_t2(int mem, const MinArgs* a, int n_clusters, int C, int npc,
+                              size_t smem, cudaStream_t s, int* max_clusters);
+cudaError_t run_mem_3_mixed_t2(int mem, const MinArgs* a, int n_clusters, int C, int npc,
+                               size_t smem, cudaStream_t s, int* max_clusters);
 
 }  // namespace aqs

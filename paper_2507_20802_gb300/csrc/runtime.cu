@@ -77,7 +77,14 @@ struct aqs_system {
   // choices made so far, keyed by (replicas in flight, largest N)
   int64_t tune_iters = 0;
   bool tuning = false;
-  std::map<std::pair<int, int64_t>, std::pair<int, int>> tuned;  // -> (C, staging)
+  struct Tuned {
+    int C, staging, tpa;
+  };
+  std::map<std::pair<int, int64_t>, Tuned> tuned;
+  // threads per atom of the force phase (1 or 2; the autotuner may choose 2
+  // where 2 npc threads fit a CTA); tpa_user marks a caller's choice
+  int tpa = 1;
+  bool tpa_user = false;
   // staging mode of the minimiser launches (-1: automatic); staging_user marks
   // a mode the caller fixed, which the tuner leaves alone
   int staging = -1;
@@ -581,10 +588,11 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
       if (it == s->tuned.end()) {
         int best = 0, mode = -1;
         AQS_TRY(tune_clusters(s, f, mask, s->tune_iters, &best, &mode, nullptr, nullptr));
-        s->tuned[key] = std::make_pair(best, mode);
+        s->tuned[key] = aqs_system::Tuned{best, mode, s->tpa};
       } else {
-        if (!s->staging_user) s->staging = it->second.second;
-        AQS_TRY(apply_cluster(s, reps, it->second.first));
+        if (!s->staging_user) s->staging = it->second.staging;
+        if (!s->tpa_user) s->tpa = it->second.tpa;
+        AQS_TRY(apply_cluster(s, reps, it->second.C));
       }
     }
   }
@@ -668,10 +676,9 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
     }
     CUDA_TRY(cudaMemcpyAsync(s->d_work, order_work.data(), sizeof(int) * order_work.size(),
                              cudaMemcpyHostToDevice, s->stream));
-    if (!s->lean32) {
+    if (!s->lean32) {  // first lean launch of this system
       bool lean = false;
-      for (int r : todo)
-        lean = lean || minimize_is_lean(s->dim, minimize_atoms_per_thread(s->dim, s->geom[r].npc));
+      for (int r : todo) lean = lean || minimize_launch_is_lean(s->dim, s->geom[r].npc, s->tpa);
       if (lean) {
         AQS_TRY(alloc_arr(s, &s->lean32, (size_t)15 * s->ntot));
         AQS_TRY(alloc_arr(s, &s->lean64, (size_t)3 * s->ntot));
@@ -710,7 +717,7 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
         CUDA_TRY(cudaStreamWaitEvent(st, s->aux_ev[4], 0));
       }
       CUDA_TRY(launch_minimize(s->dim, s->prec == AQS_MIXED, a, groups[gi].second, C, npc, nrep,
-                               s->cap, st, s->staging));
+                               s->cap, st, s->staging, s->tpa));
       if (multi) CUDA_TRY(cudaEventRecord(s->aux_ev[gi % 4], st));
       if (multi && (gi % 4 == 3 || gi + 1 == groups.size()))
         for (size_t k = 0; k <= gi % 4; k++) CUDA_TRY(cudaStreamWaitEvent(s->stream, s->aux_ev[k], 0));
@@ -1049,6 +1056,8 @@ aqs_status ensure_chains(aqs_system* s, int src, int P) {
   c->launch_budget = s->launch_budget;
   c->staging = s->staging_user ? s->staging : -1;
   c->staging_user = s->staging_user;
+  c->tpa = s->tpa_user ? s->tpa : 1;
+  c->tpa_user = s->tpa_user;
   s->chains = c;
   return AQS_OK;
 }
@@ -1849,7 +1858,7 @@ aqs_status aqs_autotune_clusters(aqs_system* s, const aqs_fire_params* f, int64_
       nmax = std::max(nmax, s->n[r]);
       cnt++;
     }
-  if (best > 0) s->tuned[std::make_pair(cnt, nmax)] = std::make_pair(best, mode);
+  if (best > 0) s->tuned[std::make_pair(cnt, nmax)] = aqs_system::Tuned{best, mode, s->tpa};
   if (best_cluster) *best_cluster = best;
   if (best_staging) *best_staging = mode;
   return AQS_OK;
@@ -1861,6 +1870,21 @@ aqs_status aqs_set_launch_budget(aqs_system* s, int64_t iters) {
   if (s->chains) s->chains->launch_budget = iters;
   return AQS_OK;
 }
+
+aqs_status aqs_set_threads_per_atom(aqs_system* s, int tpa) {
+  if (!s || tpa < 0 || tpa > 2) return fail(AQS_ERR_INVALID_ARG, "threads per atom must be 0, 1 or 2");
+  s->tpa = tpa == 0 ? 1 : tpa;
+  s->tpa_user = tpa != 0;
+  s->tuned.clear();
+  if (s->chains) {
+    s->chains->tpa = s->tpa;
+    s->chains->tpa_user = s->tpa_user;
+    s->chains->tuned.clear();
+  }
+  return AQS_OK;
+}
+
+int aqs_threads_per_atom(const aqs_system* s) { return s ? s->tpa : 0; }
 
 aqs_status aqs_set_staging(aqs_system* s, int mode) {
   if (!s || mode < -1 || mode >= kNumStaging)
@@ -2041,7 +2065,7 @@ bool cluster_feasible(const aqs_system* s, const std::vector<int>& reps, int C) 
     const int64_t npc = (s->n[r] + C - 1) / C;
     if (npc > 4096 || (C > 1 && s->n[r] < 32 * (int64_t)C)) return false;
     if (minimize_max_active_clusters(s->dim, s->prec == AQS_MIXED, C, (int)npc, (int)s->n[r],
-                                     s->nt, s->cap, s->staging) <= 0)
+                                     s->nt, s->cap, s->staging, s->tpa) <= 0)
       return false;
   }
   return true;
@@ -2107,40 +2131,50 @@ aqs_status tune_clusters(aqs_system* s, const aqs_fire_params* f, const std::vec
   ft.max_iter = iters;
   aqs_fire_params fw = ft;
   fw.max_iter = std::min<int64_t>(iters, 32);
-  const int saved_override = s->C_override, saved_staging = s->staging;
+  const int saved_override = s->C_override, saved_staging = s->staging, saved_tpa = s->tpa;
   s->tuning = true;
-  if (!s->staging_user) s->staging = -1;
-  int bestC = 0, bestM = s->staging;
+  int bestC = 0, bestM = s->staging, bestTPA = s->tpa;
   double bestT = 1e300;
+  // time per iteration of every candidate: [C][tpa - 1][mode]
+  std::vector<double> table((size_t)(kMaxCluster + 1) * 2 * kNumStaging, -1.0);
   aqs_status err = AQS_OK;
   for (int C = 1; C <= kMaxCluster && err == AQS_OK; C++) {
-    if (!cluster_feasible(s, reps, C)) continue;
-    double ms = 0.0;
-    if ((err = time_candidate(s, ft, fw, mask, reps, tilt, C, &ms)) != AQS_OK) break;
-    if (ms_per_iter) ms_per_iter[C] = ms;
-    if (ms < bestT) {
-      bestT = ms;
-      bestC = C;
-    }
-  }
-  if (err == AQS_OK && bestC > 0 && !s->staging_user) {
-    const int npc = (int)((nmax + bestC - 1) / bestC);
-    for (int m = 0; m < kNumStaging && err == AQS_OK; m++) {
-      if (minimize_staging(s->dim, npc, (int)nmax, s->nt, s->cap, m) != m) continue;
-      s->staging = m;
-      if (!cluster_feasible(s, reps, bestC)) continue;
-      double ms = 0.0;
-      if ((err = time_candidate(s, ft, fw, mask, reps, tilt, bestC, &ms)) != AQS_OK) break;
-      if (ms_per_staging) ms_per_staging[m] = ms;
-      if (ms < bestT) {
-        bestT = ms;
-        bestM = m;
+    const int npc = (int)((nmax + C - 1) / C);
+    // threads per atom of the force phase ("atoms per warp" 32 or 16), unless
+    // the caller fixed it
+    for (int tpa = 1; tpa <= 2 && err == AQS_OK; tpa++) {
+      if (s->tpa_user && tpa != saved_tpa) continue;
+      if (tpa == 2 && minimize_tpa(npc, 2) != 2) continue;
+      // every staging mode that fits: the mode decides the shared memory of
+      // a CTA and with it how many CTAs (of different clusters) share an SM,
+      // so it decides how many clusters are resident at once
+      for (int m = 0; m < kNumStaging && err == AQS_OK; m++) {
+        if (s->staging_user && m != saved_staging) continue;
+        if (minimize_staging(s->dim, npc, (int)nmax, s->nt, s->cap, m) != m) continue;
+        s->tpa = tpa;
+        s->staging = m;
+        if (!cluster_feasible(s, reps, C)) continue;
+        double ms = 0.0;
+        if ((err = time_candidate(s, ft, fw, mask, reps, tilt, C, &ms)) != AQS_OK) break;
+        table[((size_t)C * 2 + (tpa - 1)) * kNumStaging + m] = ms;
+        if (ms_per_iter && (ms_per_iter[C] < 0.0 || ms < ms_per_iter[C])) ms_per_iter[C] = ms;
+        if (ms < bestT) {
+          bestT = ms;
+          bestC = C;
+          bestTPA = tpa;
+          bestM = m;
+        }
       }
     }
   }
+  if (ms_per_staging && bestC > 0)
+    for (int m = 0; m < kNumStaging; m++)
+      ms_per_staging[m] = table[((size_t)bestC * 2 + (bestTPA - 1)) * kNumStaging + m];
+  if (s->staging_user) bestM = saved_staging;
   s->tuning = false;
   s->C_override = saved_override;
   s->staging = err == AQS_OK ? bestM : saved_staging;
+  s->tpa = err == AQS_OK ? bestTPA : saved_tpa;
   for (int r : reps) {
     const int C = (err == AQS_OK && bestC > 0) ? bestC : c0[r];
     s->geom[r].C = C;

@@ -29,6 +29,8 @@ Each file is an .npz of FP64/int arrays:
 * glass_sl_n400_s0.npz, aqs_sl_n400_s0.npz -- the paper's S/L glass (N = 400,
   density 1, Sec. 2.2) quenched by the oracle, and 20 sequential AQS steps
   of the paper's increment dgamma = 1/200 (Sec. 4).
+* aqs_sl_n400_s0_g1.npz -- the paper's whole protocol on that glass: 200
+  steps of dgamma = 1/200 to gamma = 1 (Sec. 2.2, Fig. 2b).
 
 Usage: python tests/golden/make_golden.py [name ...]   (default: all)
 """
@@ -162,6 +164,13 @@ def job_aqssl400():
     r = oracle.aqs(_pot_sl(), _fire(), g["x"], g["types"], g["H"], 1.0 / 200.0, 20)
     assert r["status"] == 0
     np.savez(os.path.join(HERE, "aqs_sl_n400_s0.npz"), dgamma=1.0 / 200.0, n_steps=20, **r)
+
+
+def job_aqssl400full():
+    g = glass_sl(400, 0)
+    r = oracle.aqs(_pot_sl(), _fire(), g["x"], g["types"], g["H"], 1.0 / 200.0, 200)
+    assert r["status"] == 0
+    np.savez(os.path.join(HERE, "aqs_sl_n400_s0_g1.npz"), dgamma=1.0 / 200.0, n_steps=200, **r)
 
 
 JOBS = {k[4:]: v for k, v in globals().items() if k.startswith("job_")}

@@ -270,6 +270,44 @@ def test_full_size_workload_properties(A, syn):
         assert np.sqrt((Fr * Fr).sum(1)).max() < 1e-10
 
 
+def test_benchmark_pass_spot_checked_by_the_oracle(A, orc, syn):
+    """One pass of the benchmark's Algorithm 1 (N = 4096 glass, P = 16,
+    K = 10, dgamma = 1e-4, mixed precision, autotuned launch) against plain
+    sequential FP64 AQS of the same glass, with the oracle as the judge: the
+    oracle's own FP64 forces vanish (|F|max < 1e-10) at the pass's r_star and
+    at the sequential run's state, the oracle's energy is the one the
+    library reports, and the accepted steps follow the sequential path
+    (energies 1e-6 per atom, identical events) as far as it was run.  (The
+    all-pairs oracle needs ~1.5 h of one host core to re-minimise one N = 4096
+    step, so the re-minimisation is the library's FP64 path.)"""
+    x, t, H = syn.random_glass_start(4096, 2, seed=0)
+    g = make_system(A, syn, x, t, H, A.AQS_FP64)
+    assert g.minimize(A.fire_params(max_iter=2_000_000))[0]["status"] == 0
+    xq, Hq = g.positions(), g.box()
+    g.close()
+    pot = oracle_pot(orc, syn, 2)
+    s = make_system(A, syn, xq, t, Hq, A.AQS_MIXED)
+    s.set_autotune(200)
+    r = s.parallel_step(1e-4, 10, 16, 160, max_iterations=1)
+    q = int(r["accepted"])
+    assert q >= 10 and r["iterations"] == 1
+    x_star, H_star = s.positions(), s.box()
+    Eo, Fo, _ = orc.energy_forces(pot, x_star, t, H_star)
+    assert np.sqrt((Fo * Fo).sum(1)).max() < 1e-10
+    assert Eo / 4096 == pytest.approx(r["E"][-1] / 4096, rel=1e-9)
+    m = min(q, 30)
+    b = make_system(A, syn, xq, t, Hq, A.AQS_FP64)
+    out = b.run_sequential(1e-4, m)
+    np.testing.assert_allclose(r["E"][:m], out["E"][:, 0], rtol=1e-6)
+    assert np.array_equal(r["D"][:m] > EV_THR, out["D"][:, 0] > EV_THR)
+    _, Fb, _ = orc.energy_forces(pot, b.positions(), t, b.box())
+    assert np.sqrt((Fb * Fb).sum(1)).max() < 1e-10
+    if q == m:
+        assert orc.max_rel_disp(x_star, b.positions(), H_star) < 1e-6
+    b.close()
+    s.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_quench_from_random_start_converges(A, syn, prec):
     """Overlapping random starts (forces ~1e16) must be handled in both modes:
