@@ -680,6 +680,10 @@ def run_tune_table(args):
         s.shear(np.arange(R) * K_FINE * DGAMMA)
         s.minimize()
         s.shear(np.full(R, DGAMMA))
+        if R == P_CHAINS:
+            occ = {m: {c: s.max_active_clusters(c, m) for c in range(1, 17)}
+                   for m in (-1, 0, 1, 2, 3)}
+            rows.append({"max_active_clusters_by_staging_and_C": occ})
         for tpa in (1, 2, 0):
             s.set_threads_per_atom(tpa)
             C, mode, msC, msM = s.autotune(iters=args.tune_iters)

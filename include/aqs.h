@@ -421,6 +421,10 @@ aqs_status aqs_set_launch_budget(aqs_system* sys, int64_t iters);
  * within rounding (the force sums are added in another order). */
 aqs_status aqs_set_threads_per_atom(aqs_system* sys, int tpa);
 int aqs_threads_per_atom(const aqs_system* sys);
+/* How many clusters of C CTAs of this replica's minimiser launch the device
+ * can hold at once (cudaOccupancyMaxActiveClusters) for a staging mode
+ * (-1 automatic) and threads per atom; -1 on a bad argument. */
+int aqs_max_active_clusters(const aqs_system* sys, int replica, int C, int staging, int tpa);
 /* Fixes the staging mode (0..3) of this system and its chains, or -1 for the
  * automatic choice.  AQS_ERR_INVALID_ARG outside -1..3. */
 aqs_status aqs_set_staging(aqs_system* sys, int mode);

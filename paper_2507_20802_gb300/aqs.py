@@ -141,6 +141,7 @@ _SIGS = {
     "aqs_set_launch_budget": (C.c_int, [C.c_void_p, C.c_int64]),
     "aqs_set_threads_per_atom": (C.c_int, [C.c_void_p, C.c_int]),
     "aqs_threads_per_atom": (C.c_int, [C.c_void_p]),
+    "aqs_max_active_clusters": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
     "aqs_set_staging": (C.c_int, [C.c_void_p, C.c_int]),
     "aqs_staging": (C.c_int, [C.c_void_p, C.c_int]),
     "aqs_set_kernel_timing": (None, [C.c_int]),
@@ -569,6 +570,9 @@ class System:
 
     def threads_per_atom(self):
         return lib().aqs_threads_per_atom(self.h)
+
+    def max_active_clusters(self, C, staging=-1, tpa=1, replica=0):
+        return lib().aqs_max_active_clusters(self.h, replica, C, staging, tpa)
 
     def set_staging(self, mode):
         check(lib().aqs_set_staging(self.h, int(mode)))

@@ -1886,6 +1886,15 @@ aqs_status aqs_set_threads_per_atom(aqs_system* s, int tpa) {
 
 int aqs_threads_per_atom(const aqs_system* s) { return s ? s->tpa : 0; }
 
+int aqs_max_active_clusters(const aqs_system* s, int replica, int C, int staging, int tpa) {
+  if (!s || replica < 0 || replica >= s->R || C < 1 || C > kMaxCluster) return -1;
+  const int64_t n = s->n[replica];
+  const int npc = (int)((n + C - 1) / C);
+  if (npc > 4096) return 0;
+  return minimize_max_active_clusters(s->dim, s->prec == AQS_MIXED, C, npc, (int)n, s->nt, s->cap,
+                                      staging, tpa < 1 ? 1 : tpa);
+}
+
 aqs_status aqs_set_staging(aqs_system* s, int mode) {
   if (!s || mode < -1 || mode >= kNumStaging)
     return fail(AQS_ERR_INVALID_ARG, "set_staging: mode must be -1 or 0..%d", kNumStaging - 1);

@@ -453,6 +453,37 @@ def test_paper_sl_glass_trajectory_matches_golden(A, syn, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_paper_protocol_to_gamma_one_matches_golden(A, syn, prec):
+    """The paper's whole protocol on its S/L glass: 200 steps of 1/200 to
+    gamma = 1 (Sec. 2.2, Fig. 2b) by sequential AQS and by Algorithm 1
+    (P = 8, K = 6), both against the stored oracle run of sequential AQS: the
+    per-step energies, non-affine displacements and the final configuration
+    (the paper reports equal final configurations for every run)."""
+    g = load_golden("glass_sl_n400_s0.npz")
+    gold = load_golden("aqs_sl_n400_s0_g1.npz")
+    P = A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED
+    rel = 1e-9 if prec == "fp64" else 1e-6
+    n, dg = int(gold["n_steps"]), float(gold["dgamma"])
+
+    def mk():
+        return A.System(np.asarray(g["x"], float), g["types"], g["H"][None], [len(g["x"])],
+                        syn.SL_SIGMA, syn.SL_EPS, syn.RC_FACTOR, precision=P)
+    s = mk()
+    out = s.run_sequential(dg, n)
+    np.testing.assert_allclose(out["E"][:, 0], gold["E"], rtol=rel)
+    np.testing.assert_allclose(out["D"][:, 0], gold["D"], rtol=1e-4, atol=1e-9)
+    assert mi_disp(s.positions(), gold["x"], gold["H"]) < 1e-6
+    np.testing.assert_allclose(s.box(), gold["H"], rtol=1e-12)
+    s.close()
+    s = mk()
+    r = s.parallel_step(dg, 6, 8, n)
+    assert r["accepted"] == n
+    np.testing.assert_allclose(r["E"], gold["E"], rtol=rel)
+    assert mi_disp(s.positions(), gold["x"], gold["H"]) < 1e-6
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_dynamic_k_matches_golden(A, syn, glass256, prec):
     """Algorithm 1 with dynamic K (K = 3, K_max = 12, P = 4, dgamma = 1/200,
     30 steps): the chain length of every pass, the decision log and the
