@@ -68,13 +68,13 @@ KERNEL_FLOP32_PER_VISIT = 62
 FLOP64_PER_PAIR = 32
 # DRAM bytes (read + write) of the dominant kernel from one ncu capture each
 # (--set full, clocks unlocked), for the roofline's "traffic"; a capture is
-# valid only for the kernel version it was taken on.
-#   Algorithm 1 (2D, N = 4096): one level-II chain launch of 45.6 ms, on chip
-TRAFFIC_CFG1_PER_LAUNCH = 11_975_680
-#   3D (N = 65536): the timed launch of 6 replicas x 200 iterations (36.10 GB
-#   read + 0.42 GB written), per replica-iteration; the bench scales it by the
-#   replica-iterations of its launch
-TRAFFIC_3D_PER_REPLICA_ITER = 30_438_000
+# valid only for the kernel version it was taken on (None: not captured on
+# the current kernel).
+#   Algorithm 1 (2D, N = 4096): one level-II chain launch; the kernel runs from
+#   L2, and its DRAM traffic is the working set read once per launch
+TRAFFIC_CFG1_PER_LAUNCH = 10_614_016
+#   3D (N = 65536), per replica-iteration of the timed launch
+TRAFFIC_3D_PER_REPLICA_ITER = None
 
 CONFIG = {"workload": "2D binary LJ glass (65:35, rho=1.2), N=4096, Algorithm 1 with P=16 "
                       "chains of K=10 fine steps, dgamma=1e-4, FIRE to |F|max<1e-10, mixed "
@@ -1010,7 +1010,8 @@ def main():
                 "flop_per_list_entry": FLOP32_PER_PAIR,
                 "kernel_flop_per_visit": KERNEL_FLOP32_PER_VISIT,
                 "traffic": TRAFFIC_CFG1_PER_LAUNCH,
-                "traffic_note": "bytes per launch, ncu capture of one level-II chain launch",
+                "traffic_note": "DRAM bytes of one captured level-II chain launch (the L2-resident "
+                                "working set, read once per launch)",
                 "kernel": "k_minimize<2,mixed>",
                 "kernel_share_of_step": kern_s / secs if secs > 0 else None,
                 "fp64_tflops": flop64 / kern_s / 1e12 if kern_s > 0 else 0.0,

@@ -218,19 +218,28 @@ void cell_widths(int D, const double* H, double* w) {
   if (D == 3) w[2] = H[8];
 }
 
-// Cluster size for R concurrently minimised replicas of n atoms: spread the
-// replicas over the device's SMs (one CTA per SM), at most 16 CTAs per
-// replica, at least 32 atoms per CTA and at most 4096.  The cluster
-// scheduler's own limit is checked with the occupancy API; a size it cannot
-// place is skipped.
+// Cluster size for R concurrently minimised replicas of n atoms: the largest
+// C (at most 16, at least 32 atoms and at most 4096 atoms per CTA) at which
+// the device holds all R clusters at once (cudaOccupancyMaxActiveClusters;
+// clusters are placed per GPC, so e.g. 23 clusters of 6 CTAs fit a GB300 but
+// only 15 of 7-9).  When no size holds all R, the size with the most resident
+// CTAs.
 int auto_cluster(int dim, bool mixed, int R, int64_t n, int nt, int cap) {
-  int C = std::min(kMaxCluster, std::max(1, sm_count() / std::max(1, R)));
-  C = (int)std::min<int64_t>(C, std::max<int64_t>(1, n / 32));
-  while ((n + C - 1) / C > 4096 && C < kMaxCluster) C++;
-  for (; C > 1; C--) {
-    int64_t npc = (n + C - 1) / C;
-    if (minimize_max_active_clusters(dim, mixed, C, (int)npc, (int)n, nt, cap) > 0) break;
+  const int Cmax = (int)std::min<int64_t>(kMaxCluster, std::max<int64_t>(1, n / 32));
+  int fallback = 0, most = -1;
+  for (int C = Cmax; C >= 1; C--) {
+    const int64_t npc = (n + C - 1) / C;
+    if (npc > 4096) break;
+    const int m = minimize_max_active_clusters(dim, mixed, C, (int)npc, (int)n, nt, cap);
+    if (m >= std::max(1, R)) return C;
+    if (m > 0 && (int64_t)m * C > most) {
+      most = m * C;
+      fallback = C;
+    }
   }
+  if (fallback > 0) return fallback;
+  int C = 1;
+  while ((n + C - 1) / C > 4096 && C < kMaxCluster) C++;
   return C;
 }
 
@@ -498,32 +507,6 @@ MinArgs min_args(aqs_system* s, const aqs_fire_params* f) {
   a.hist_stride = 0;
   for (int k = 0; k < AQS_MAX_TYPES * AQS_MAX_TYPES; k++) a.rl2f[k] = s->rl2f[k];
   return a;
-}
-
-// Non-affine displacement max_a |(x_a - xs_a) - mean| of each listed replica.
-aqs_status nonaffine(aqs_system* s, const std::vector<int>& reps, std::vector<double>& out) {
-  std::vector<CmpJob> jobs(reps.size());
-  for (size_t k = 0; k < reps.size(); k++) {
-    int r = reps[k];
-    CmpJob& J = jobs[k];
-    J.a = s->x + s->off[r];
-    J.b = s->xs + s->off[r];
-    J.sa = 1;
-    J.sc = s->ntot;
-    J.sb = 1;
-    J.sc2 = s->ntot;
-    std::memcpy(J.H, s->geom[r].H, sizeof(J.H));
-    J.n = (int)s->n[r];
-  }
-  out.assign(reps.size(), 0.0);
-  if (reps.empty()) return AQS_OK;
-  CUDA_TRY(cudaMemcpyAsync(s->d_jobs, jobs.data(), sizeof(CmpJob) * jobs.size(),
-                           cudaMemcpyHostToDevice, s->stream));
-  CUDA_TRY(launch_compare(s->dim, s->d_jobs, (int)jobs.size(), s->d_cmp, s->stream));
-  CUDA_TRY(cudaMemcpyAsync(out.data(), s->d_cmp, sizeof(double) * reps.size(),
-                           cudaMemcpyDeviceToHost, s->stream));
-  CUDA_TRY(cudaStreamSynchronize(s->stream));
-  return AQS_OK;
 }
 
 // Per-replica job: nsteps fine steps of increment dgamma (affine map, then
