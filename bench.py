@@ -73,8 +73,9 @@ FLOP64_PER_PAIR = 32
 #   Algorithm 1 (2D, N = 4096): one level-II chain launch; the kernel runs from
 #   L2, and its DRAM traffic is the working set read once per launch
 TRAFFIC_CFG1_PER_LAUNCH = 10_614_016
-#   3D (N = 65536), per replica-iteration of the timed launch
-TRAFFIC_3D_PER_REPLICA_ITER = None
+#   3D (N = 65536), per replica-iteration of the timed launch (6 replicas x
+#   200 iterations: 36.16 GB read + 0.52 GB written)
+TRAFFIC_3D_PER_REPLICA_ITER = 30_570_000
 
 CONFIG = {"workload": "2D binary LJ glass (65:35, rho=1.2), N=4096, Algorithm 1 with P=16 "
                       "chains of K=10 fine steps, dgamma=1e-4, FIRE to |F|max<1e-10, mixed "
