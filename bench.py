@@ -70,9 +70,11 @@ FLOP64_PER_PAIR = 32
 # (--set full, clocks unlocked), for the roofline's "traffic"; a capture is
 # valid only for the kernel version it was taken on (None: not captured on
 # the current kernel).
-#   Algorithm 1 (2D, N = 4096): one level-II chain launch; the kernel runs from
-#   L2, and its DRAM traffic is the working set read once per launch
-TRAFFIC_CFG1_PER_LAUNCH = 10_614_016
+#   Algorithm 1 (2D, N = 4096): one level-II chain launch, per barrier mode of
+#   the chains (thread-block clusters, or one cooperative launch with grid
+#   barriers); the kernel runs from L2, and its DRAM traffic is the working
+#   set read once per launch
+TRAFFIC_CFG1_PER_LAUNCH = {"cluster": 10_614_016, "grid_barrier": None}
 #   3D (N = 65536), per replica-iteration of the timed launch (6 replicas x
 #   200 iterations: 36.16 GB read + 0.52 GB written)
 TRAFFIC_3D_PER_REPLICA_ITER = 30_570_000
@@ -685,15 +687,18 @@ def run_tune_table(args):
             occ = {m: {c: s.max_active_clusters(c, m) for c in range(1, 17)}
                    for m in (-1, 0, 1, 2, 3)}
             rows.append({"max_active_clusters_by_staging_and_C": occ})
-        for tpa in (1, 2, 0):
-            s.set_threads_per_atom(tpa)
-            C, mode, msC, msM = s.autotune(iters=args.tune_iters)
-            rows.append({"replicas": R, "threads_per_atom": {1: "1", 2: "2", 0: "tuned"}[tpa],
-                         "chosen_threads_per_atom": s.threads_per_atom(), "best_C": C,
-                         "staging": mode,
-                         "us_per_iter_by_C": {c: round(v * 1e3, 2) for c, v in msC.items()},
-                         "us_per_iter_by_staging": {m: round(v * 1e3, 2)
-                                                    for m, v in msM.items()}})
+        for gb in (False, True):
+            s.set_grid_barrier(gb)
+            for tpa in ((1, 2, 0) if not gb else (1,)):
+                s.set_threads_per_atom(tpa)
+                C, mode, msC, msM = s.autotune(iters=args.tune_iters)
+                rows.append({"replicas": R, "grid_barrier": gb,
+                             "threads_per_atom": {1: "1", 2: "2", 0: "tuned"}[tpa],
+                             "chosen_threads_per_atom": s.threads_per_atom(), "best_C": C,
+                             "staging": mode,
+                             "us_per_iter_by_C": {c: round(v * 1e3, 2) for c, v in msC.items()},
+                             "us_per_iter_by_staging": {m: round(v * 1e3, 2)
+                                                        for m, v in msM.items()}})
         s.close()
     print(json.dumps({"metric": "minimiser time per FIRE iteration by launch configuration",
                       "unit": "us", "config": CONFIG, "iters_per_candidate": args.tune_iters,
@@ -863,6 +868,8 @@ def main():
                     help="> 0: Metric 1 over glasses of seeds 0..n-1 (mean and std)")
     ap.add_argument("--launch-budget", type=int, default=2048,
                     help="FIRE iterations per persistent launch")
+    ap.add_argument("--grid-barrier", action="store_true",
+                    help="the chains in one cooperative launch with global-memory barriers")
     ap.add_argument("--autotune", type=int, default=300,
                     help="FIRE iterations per autotuner candidate (0: size rule only)")
     ap.add_argument("--quench-iters", type=int, default=400000)
@@ -908,6 +915,8 @@ def main():
     g.close()
     s = A.System(xq, t, Hq[None], [N_ATOMS], syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
                  precision=A.AQS_MIXED)
+    if args.grid_barrier:
+        s.set_grid_barrier(True)
     if args.autotune > 0:
         # the chains tune cluster size and staging during the first (untimed)
         # warm-up pass
@@ -1006,14 +1015,16 @@ def main():
     flop64 = st["pairs64"] * FLOP64_PER_PAIR
     achieved = flop32 / kern_s / 1e12 if kern_s > 0 else 0.0
     peak32, n_sm, mhz = fp32_peak_tflops()
+    chain_mode = "grid_barrier" if s.grid_barrier(chains=True) == 1 else "cluster"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak32,
                 "unit": "TFLOP/s", "frac": achieved / peak32,
                 "flop_per_list_entry": FLOP32_PER_PAIR,
                 "kernel_flop_per_visit": KERNEL_FLOP32_PER_VISIT,
-                "traffic": TRAFFIC_CFG1_PER_LAUNCH,
+                "traffic": TRAFFIC_CFG1_PER_LAUNCH[chain_mode],
                 "traffic_note": "DRAM bytes of one captured level-II chain launch (the L2-resident "
-                                "working set, read once per launch)",
+                                "working set, read once per launch), %s kernel" % chain_mode,
                 "kernel": "k_minimize<2,mixed>",
+                "barrier_mode": chain_mode,
                 "kernel_share_of_step": kern_s / secs if secs > 0 else None,
                 "fp64_tflops": flop64 / kern_s / 1e12 if kern_s > 0 else 0.0,
                 "launches": st["launches"], "avg_launch_ms": st["kernel_ms"] / max(1, st["launches"]),

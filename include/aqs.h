@@ -91,8 +91,10 @@ typedef struct {
   int cluster_size;        /* CTAs per replica (1..16); <= 0 selects automatically */
   void* stream;            /* cudaStream_t for all work; NULL = legacy default stream */
   /* optional device allocator (e.g. a framework's caching allocator); both
-   * NULL selects cudaMalloc/cudaFree.  The library never frees what it did
-   * not allocate. */
+   * NULL selects cudaMalloc/cudaFree.  Blocks must be 16-byte aligned (the
+   * kernels use 16-byte vector and 8-byte atomic accesses); a misaligned
+   * block fails the call with AQS_ERR_OOM.  The library never frees what it
+   * did not allocate. */
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, void* ctx);
   void* alloc_ctx;
@@ -383,10 +385,12 @@ aqs_status aqs_energy_forces_noalloc(int dim, int64_t n, const double* pos, cons
  * mask[r] != 0 (NULL = all): every feasible C in 1..16 (at most 4096 and at
  * least 32 atoms per CTA, at least one cluster resident), each with every
  * staging mode that fits and with one and (where it fits) two threads per
- * atom in the force phase (the staging mode sets a CTA's shared memory and so
+ * atom in the force phase, and the same sizes again as one cooperative launch
+ * with grid barriers (aqs_set_grid_barrier; staging modes 0 and 3) (the staging mode sets a CTA's shared memory and so
  * how many CTAs of different clusters share an SM, i.e. how many replicas'
  * clusters are resident at once).  Keeps the fastest (C, staging, threads per
- * atom), except what aqs_set_staging / aqs_set_threads_per_atom fixed;
+ * atom, barrier mode), except what aqs_set_staging / aqs_set_threads_per_atom /
+ * aqs_set_grid_barrier fixed;
  * ms_per_iter[C] is the fastest candidate at C.
  * Outputs, each may be NULL: *best_cluster, *best_staging;
  * ms_per_iter[17] (entry C: wall time per iteration in ms, -1 if C was not
@@ -421,6 +425,23 @@ aqs_status aqs_set_launch_budget(aqs_system* sys, int64_t iters);
  * within rounding (the force sums are added in another order). */
 aqs_status aqs_set_threads_per_atom(aqs_system* sys, int tpa);
 int aqs_threads_per_atom(const aqs_system* sys);
+/* on = 1: the minimiser runs the replicas' CTAs in one cooperative launch
+ * without thread-block clusters; the CTAs of a replica synchronise through a
+ * barrier in global memory (bounded waits: a wait that runs out ends the
+ * call with AQS_ERR_TIMEOUT) and read neighbour records from global memory
+ * (staging modes 0 and 3).  The device holds clusters per GPC, which limits
+ * how many replicas fit at a given cluster size (e.g. 15 clusters of 7-9 CTAs
+ * on a GB300); a cooperative launch is limited only by resident CTAs.  One
+ * cluster size for all replicas of a launch.  on = 0: thread-block clusters;
+ * on = -1 (the default): the autotuner (aqs_set_autotune) times both and keeps
+ * the faster, clusters without it.  Applies to the system and its chains.
+ * Results agree within rounding with the cluster launches. */
+aqs_status aqs_set_grid_barrier(aqs_system* sys, int on);
+/* The barrier mode the minimiser launches use: of this system (of_chains =
+ * 0) or of its level-II chains (of_chains = 1): 1 grid barriers, 0 clusters
+ * (after autotuning, the mode it kept); -1 if the chains have not run yet or
+ * sys is NULL. */
+int aqs_grid_barrier(const aqs_system* sys, int of_chains);
 /* How many clusters of C CTAs of this replica's minimiser launch the device
  * can hold at once (cudaOccupancyMaxActiveClusters) for a staging mode
  * (-1 automatic) and threads per atom; -1 on a bad argument. */

@@ -142,6 +142,8 @@ _SIGS = {
     "aqs_set_threads_per_atom": (C.c_int, [C.c_void_p, C.c_int]),
     "aqs_threads_per_atom": (C.c_int, [C.c_void_p]),
     "aqs_max_active_clusters": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "aqs_set_grid_barrier": (C.c_int, [C.c_void_p, C.c_int]),
+    "aqs_grid_barrier": (C.c_int, [C.c_void_p, C.c_int]),
     "aqs_set_staging": (C.c_int, [C.c_void_p, C.c_int]),
     "aqs_staging": (C.c_int, [C.c_void_p, C.c_int]),
     "aqs_set_kernel_timing": (None, [C.c_int]),
@@ -570,6 +572,14 @@ class System:
 
     def threads_per_atom(self):
         return lib().aqs_threads_per_atom(self.h)
+
+    def set_grid_barrier(self, on):
+        """True / False fixes the barrier mode; None lets the autotuner choose."""
+        check(lib().aqs_set_grid_barrier(self.h, -1 if on is None else (1 if on else 0)))
+
+    def grid_barrier(self, chains=False):
+        """1 grid barriers, 0 clusters, -1 chains not run yet."""
+        return lib().aqs_grid_barrier(self.h, 1 if chains else 0)
 
     def max_active_clusters(self, C, staging=-1, tpa=1, replica=0):
         return lib().aqs_max_active_clusters(self.h, replica, C, staging, tpa)

@@ -59,9 +59,18 @@ bool minimize_launch_is_lean(int dim, int npc, int tpa) {
 
 static cudaError_t dispatch(int dim, bool mixed, const MinArgs* a, int n_clusters, int C, int npc,
                             int nrep, int nt, int cap, cudaStream_t s, int* max_clusters,
-                            int staging, int tpa) {
+                            int staging, int tpa, bool gb = false) {
   int mem = choose_mem(dim, npc, nrep, nt, cap, staging);
+  if (gb && mem != 0 && mem != 3)  // grid barriers read neighbour records from global memory
+    mem = minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, 3) <= kSmemLimit ? 3 : 0;
   size_t smem = minimize_smem_bytes_impl(dim, npc, nrep, nt, cap, mem);
+  if (gb) {
+    if (dim == 2)
+      return mixed ? run_mem_2_mixed_gb(mem, a, n_clusters, C, npc, smem, s, max_clusters)
+                   : run_mem_2_fp64_gb(mem, a, n_clusters, C, npc, smem, s, max_clusters);
+    return mixed ? run_mem_3_mixed_gb(mem, a, n_clusters, C, npc, smem, s, max_clusters)
+                 : run_mem_3_fp64_gb(mem, a, n_clusters, C, npc, smem, s, max_clusters);
+  }
   if (effective_tpa(npc, tpa) == 2) {
     if (dim == 2)
       return mixed ? run_mem_2_mixed_t2(mem, a, n_clusters, C, npc, smem, s, max_clusters)
@@ -77,10 +86,23 @@ static cudaError_t dispatch(int dim, bool mixed, const MinArgs* a, int n_cluster
 }
 
 cudaError_t launch_minimize(int dim, bool mixed, MinArgs a, int n_clusters, int C, int npc,
-                            int nrep, int cap, cudaStream_t s, int staging, int tpa) {
+                            int nrep, int cap, cudaStream_t s, int staging, int tpa,
+                            bool grid_barrier) {
   a.npc_launch = npc;
   a.nrep_launch = nrep;
-  return dispatch(dim, mixed, &a, n_clusters, C, npc, nrep, a.nt, cap, s, nullptr, staging, tpa);
+  return dispatch(dim, mixed, &a, n_clusters, C, npc, nrep, a.nt, cap, s, nullptr, staging,
+                  grid_barrier ? 1 : tpa, grid_barrier);
+}
+
+int minimize_max_grid_replicas(int dim, bool mixed, int C, int npc, int nrep, int nt, int cap,
+                               int staging) {
+  int m = 0;
+  if (dispatch(dim, mixed, nullptr, 1, C, npc, nrep, nt, cap, nullptr, &m, staging, 1, true) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return m;
 }
 
 int minimize_max_active_clusters(int dim, bool mixed, int C, int npc, int nrep, int nt, int cap,

@@ -54,6 +54,14 @@ struct MinArgs {
   // the kernel keeps the full cell in RepState::Hc / Hb
   const double* hist;
   int64_t hist_stride;
+  // grid-barrier launches (cooperative, no clusters): CTAs per replica,
+  // reduction partials [R][16][kNumRed], barrier words [R][2] (read as one
+  // 64-bit arrival counter per replica, 8-byte aligned, zeroed before every
+  // launch), error word (set when a barrier wait runs out)
+  int gb_C;
+  double* gb_part;
+  unsigned* gb_bar;
+  int* gb_err;
 };
 
 // Staging modes of the minimiser (where a CTA finds list rows and the
@@ -73,7 +81,12 @@ int minimize_staging(int dim, int npc, int nrep, int nt, int cap, int want);
 // tpa: threads per atom of the force phase wanted (1, or 2 where npc * 2
 // threads fit in a CTA; see minimize_tpa)
 cudaError_t launch_minimize(int dim, bool mixed, MinArgs a, int n_clusters, int C, int npc,
-                            int nrep, int cap, cudaStream_t s, int staging = -1, int tpa = 1);
+                            int nrep, int cap, cudaStream_t s, int staging = -1, int tpa = 1,
+                            bool grid_barrier = false);
+// grid-barrier launches: how many replicas of C CTAs fit the device at once
+// (cooperative launches need every CTA resident)
+int minimize_max_grid_replicas(int dim, bool mixed, int C, int npc, int nrep, int nt, int cap,
+                               int staging);
 // threads per atom a launch with npc atoms per CTA uses when `want` is asked
 int minimize_tpa(int npc, int want);
 // the launch keeps per-atom state in MinArgs::lean32 / lean64

@@ -1,0 +1,13 @@
+// minimize_3d_fp64_gb.cu -- instantiation of the persistent minimiser for
+// dimension 3, FP64 precision, with grid barriers (cooperative launch, no
+// clusters); its own unit so that the variants compile in parallel.
+#include "minimize_launch.cuh"
+
+namespace aqs {
+
+cudaError_t run_mem_3_fp64_gb(int mem, const MinArgs* a, int n_clusters, int C, int npc,
+                              size_t smem, cudaStream_t s, int* max_clusters) {
+  return run_mem<3, false, 1, true>(mem, a, n_clusters, C, npc, smem, s, max_clusters);
+}
+
+}  // namespace aqs

@@ -189,6 +189,22 @@ __device__ __forceinline__ double get_d(const float* q) {
   return __hiloint2double(__float_as_int(q[1]), __float_as_int(q[0]));
 }
 
+// Polls of a grid-barrier wait before it gives up (each an L2 round trip plus
+// a short back-off: a few seconds); a wait that runs out sets the launch's
+// error word and the replica stops.
+constexpr long long kGbSpinLimit = 1ll << 22;
+
+// Grid-barrier arrival (release: the writes before it become visible to any
+// thread that acquires the counter) and poll (acquire).
+__device__ __forceinline__ void gb_arrive(unsigned long long* p) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(p) : "memory");
+}
+__device__ __forceinline__ unsigned long long gb_poll(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // While the largest FP64 force exceeds this, mixed mode keeps evaluating in
 // FP64 (random starts and collisions), where FP32 would overflow.
 constexpr double kBigForce = 1e3;
@@ -207,12 +223,19 @@ constexpr double kBigV2 = 1e30;
 // sums its partial forces by shuffles in a fixed order; the other phases keep
 // one thread per atom.  It halves the serial pair chain of each thread and
 // doubles the warps that hide its latency.
-template <int D, bool MIXED, int APT, int MEM, int TPA>
+// GB: the C CTAs of a replica are consecutive blocks of a cooperative launch
+// (no thread-block cluster) and synchronise through a barrier in global
+// memory (MinArgs::gb_bar), with their reduction partials in global memory;
+// only the global-record staging modes (0, 3).  A cooperative launch keeps
+// every CTA resident, so the replicas' CTAs are not bound to the per-GPC
+// placement of clusters.
+template <int D, bool MIXED, int APT, int MEM, int TPA, bool GB>
 __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 : 512, 1)
     k_minimize(MinArgs A) {
+  static_assert(!GB || MEM == 0 || MEM == 3, "grid barriers need global neighbour records");
   cg::cluster_group cl = cg::this_cluster();
-  const int C = (int)cl.num_blocks();
-  const int rank = (int)cl.block_rank();
+  const int C = GB ? A.gb_C : (int)cl.num_blocks();
+  const int rank = GB ? (int)(blockIdx.x % (unsigned)C) : (int)cl.block_rank();
   const int ri = A.work[blockIdx.x / C];
   const RepGeom& g = A.geom[ri];
   RepState* st = A.state + ri;
@@ -232,8 +255,11 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
   Pub<D>* pub = reinterpret_cast<Pub<D>*>(smem_raw);  // MEM 2: whole replica, else own atoms
   Pub<D>* mine = MEM == 2 ? pub + lo : pub;
   const int pub_len = MEM == 2 ? A.nrep_launch : lstride;
-  double* red = reinterpret_cast<double*>(smem_raw + sizeof(Pub<D>) * pub_len);  // [kNumRed]
-  double* wred = red + kNumRed;                                                   // [32][kNumRed]
+  double* sred = reinterpret_cast<double*>(smem_raw + sizeof(Pub<D>) * pub_len);  // [kNumRed]
+  // this CTA's reduction partials: shared memory (read by the other CTAs of
+  // the cluster through DSMEM), or a global slot per (replica, rank) with GB
+  double* red = GB ? A.gb_part + ((int64_t)ri * kMaxCluster + rank) * kNumRed : sred;
+  double* wred = sred + kNumRed;                                                  // [32][kNumRed]
   double* off64 = wred + 32 * kNumRed;                                            // [27][3]
   float* off32 = reinterpret_cast<float*>(off64 + 27 * 3);                        // [27][3]
   float* off32l = off32 + 27 * 3 + 3;                                             // [27*3][32]
@@ -244,8 +270,41 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
   __shared__ Ctl ctl;
   __shared__ double shv[4];
   __shared__ unsigned need;  // MEM 2: bit r set if rank r owns neighbours of this CTA
-  if (tid == 0) need = 0u;
+  __shared__ int gb_abort;   // GB: a barrier of this CTA ran out of spins
+  if (tid == 0) {
+    need = 0u;
+    gb_abort = 0;
+  }
   __syncthreads();
+  // Barrier over the replica's CTAs: the cluster barrier, or with GB an
+  // arrival counter in global memory (64 bits per replica, zeroed by the host
+  // before every launch): the k-th barrier of a launch ends when the counter
+  // reaches k C.  Thread 0 arrives with a release reduction (after the CTA
+  // barrier, so it publishes the writes of every thread of the CTA) and polls
+  // with acquire loads, at most kGbSpinLimit times.
+  unsigned long long* gctr = GB ? reinterpret_cast<unsigned long long*>(A.gb_bar) + ri : nullptr;
+  unsigned long long gb_target = 0;  // thread 0: arrivals that end the next barrier
+  auto csync = [&]() {
+    if constexpr (GB) {
+      __syncthreads();
+      if (tid == 0) {
+        gb_target += (unsigned long long)C;
+        gb_arrive(gctr);
+        long long spins = 0;
+        while (gb_poll(gctr) < gb_target) {
+          if (++spins > kGbSpinLimit) {
+            gb_abort = 1;
+            atomicExch(A.gb_err, 1);
+            break;
+          }
+          if (spins > 32) __nanosleep(32);
+        }
+      }
+      __syncthreads();
+    } else {
+      cl.sync();
+    }
+  };
 
   // ---- set-up: geometry (tilt from the kernel-written state), tables ----
   double H[9], Hb[9];
@@ -274,8 +333,13 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
   make_tables();
   for (int k = tid; k < A.nt * A.nt; k += nthr) coef[k] = A.coef[k];
   if (tid < C) {
-    rpub[tid] = cl.map_shared_rank(pub, tid);
-    rred[tid] = cl.map_shared_rank(red, tid);
+    if constexpr (GB) {
+      rpub[tid] = nullptr;
+      rred[tid] = A.gb_part + ((int64_t)ri * kMaxCluster + tid) * kNumRed;
+    } else {
+      rpub[tid] = cl.map_shared_rank(pub, tid);
+      rred[tid] = cl.map_shared_rank(red, tid);
+    }
   }
   const FireDev fp = A.fire;
   // ---- the replica's job: nsteps fine steps (affine dgamma + minimisation) ----
@@ -434,7 +498,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
         if (lane == 0) red[m] = t;
       }
     }
-    cl.sync();
+    csync();
     if (warp == 0) {
       for (int m = 0; m < nv; m++) {
         double t = lane < C ? rred[lane][m] : 0.0;
@@ -445,7 +509,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
         if (lane == 0) shv[m] = t;
       }
     }
-    cl.sync();  // every CTA has read the partials before they are reused
+    csync();  // every CTA has read the partials before they are reused
     for (int m = 0; m < nv; m++) v[m] = shv[m];
   };
 
@@ -503,14 +567,14 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
       for (int c = 0; c < D; c++) qf[c] = (float)(A.x[c * N + gi] - o[c]);
       store_pub32<D>(&pubg[gi], qf, zf);
     }
-    cl.sync();
+    csync();
     // 2. histogram
 #pragma unroll
     for (int k = 0; k < APT; k++) {
       int li = tid + k * nthr;
       if (li < cnt) atomicAdd(&A.count[coff + A.cell[base + li]], 1);
     }
-    cl.sync();
+    csync();
     // 3. exclusive scan (rank 0), counts become scatter cursors
     if (rank == 0) {
       int* swsum = reinterpret_cast<int*>(wred);  // [32] warp sums, [32] carry
@@ -546,7 +610,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
       }
       if (tid == 0) A.cstart[coff + ncell] = scarry;
     }
-    cl.sync();
+    csync();
     // 4. scatter replica-local indices into the cells
 #pragma unroll
     for (int k = 0; k < APT; k++) {
@@ -556,7 +620,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
       const int p = A.cstart[coff + key] + atomicAdd(&A.count[coff + key], 1);
       A.cellatoms[aoff + p] = lo + li;
     }
-    cl.sync();
+    csync();
     // 5. deterministic order inside each cell
     for (int c = rank * nthr + tid; c < ncell; c += C * nthr) {
       const int b = A.cstart[coff + c], e = A.cstart[coff + c + 1];
@@ -570,7 +634,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
         A.cellatoms[aoff + j + 1] = v;
       }
     }
-    cl.sync();
+    csync();
     // 6. Verlet rows of the own atoms (same test as the host-side build),
     //    written to the global list and, when staged, to shared memory
     if (MEM == 2 && tid == 0) need = 0u;
@@ -628,7 +692,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
     }
     double ov[1] = {over};
     cluster_reduce(ov, 1, true);  // also orders the list writes before their use
-    return ov[0] == 0.0;
+    return ov[0] == 0.0 && !(GB && gb_abort);
   };
 
 
@@ -700,7 +764,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
     for (int k = 0; k < APT; k++)
       if (tid + k * nthr < cnt) publish64(k);
     int mode = kModeEval64;
-    cl.sync();
+    csync();
 
     for (;;) {
       if (MEM == 2) {
@@ -713,7 +777,12 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
     for (int m = 0; m < kNumRed; m++) r[m] = 0.0;
     float rf[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // DEV: fmax^2, -, |F|^2, |v|^2, max|delta|^2
     double rp = 0.0;  // DEV: the FIRE power P = F.v, summed in FP64
-#pragma unroll
+    // 3D lean launches walk their atoms one at a time (the per-atom state is in
+    // global memory, ~100 list entries give each atom's loop its own
+    // parallelism, and unrolling over atoms only lengthens live ranges at 64
+    // registers: 4 % faster); 2D lists are short, there the unrolled atoms
+    // are the parallelism
+#pragma unroll ((LEAN && D == 3) ? 1 : APT)
     for (int k = 0; k < APT; k++) {
       if constexpr (!LEAN) {
 #pragma unroll
@@ -730,7 +799,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
       int64_t gi = base + li;
       const uint32_t* row = A.nb + g.nb_off + lo + li;
       const int nn = A.nnb[gi];
-      const int ti = TPA > 1 ? A.type[gi] : ty[k];
+      const int ti = (TPA > 1 || (LEAN && D == 3)) ? A.type[gi] : ty[k];
       // per-atom state of this atom (written by the group's first lane)
       auto FDa = [&](int c) -> double& {
         if constexpr (TPA > 1) return l64[c * N + gi];
@@ -886,7 +955,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
           if (lane == 0) red[m] = t;
         }
       }
-      cl.sync();  // (A) partials of every CTA visible; all force phases done
+      csync();  // (A) partials of every CTA visible; all force phases done
       if (warp == 0) {
 #pragma unroll
         for (int m = 0; m < kNumRed; m++) {
@@ -943,7 +1012,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
         if (lane == 0)
           for (int m = 0; m < 8; m++) red32[m] = o8[m];
       }
-      cl.sync();  // (A) partials of every CTA visible; all force phases done
+      csync();  // (A) partials of every CTA visible; all force phases done
       if (warp == 0) {
         float o8[8];
         const float* rq = lane < C ? reinterpret_cast<const float*>(rred[lane]) : red32;
@@ -964,7 +1033,15 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
       bool stop = false;
       Ctl c;
       c.reset = 0;
-      if (MIXED) {
+      if (GB && gb_abort) {
+        status = AQS_ERR_TIMEOUT;
+        c.stop = 1;
+        c.move = 0;
+        c.dtf = c.ratiof = 0.f;
+        c.keepf = 1.f;
+        c.dt = c.ratio = 0.0;
+        c.keep = 1.0;
+      } else if (MIXED) {
         float fm, umax, P, F2, V2;
         bool finite;
         if (was64) {
@@ -1248,7 +1325,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
         publish64(k);
       }
     }
-      cl.sync();  // (B) new positions visible; partial slots free again
+      csync();  // (B) new positions visible; partial slots free again
     }
     // materialise x = x_ref + delta (mixed)
     if (MIXED) {
@@ -1347,7 +1424,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
       break;
     }
     if (launch_iters >= A.launch_budget) break;  // yield; the next launch starts the step
-    cl.sync();  // everybody is done with this step before the next one publishes
+    csync();  // everybody is done with this step before the next one publishes
   }
 
   // ---- exit: keep v for a resumed minimisation, store the job state ----
@@ -1387,7 +1464,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
       st->tau = W;
     }
   }
-  cl.sync();  // nobody leaves while others may still read its shared memory
+  csync();  // nobody leaves while others may still read its shared memory
 }
 
 }  // namespace aqs

@@ -45,12 +45,30 @@ inline void choose_apt(int dim, int npc, int* apt, int* threads, int tpa = 1) {
   *threads = ((t + 31) / 32) * 32;
 }
 
-template <int D, bool MIXED, int APT, int MEM, int TPA>
+template <int D, bool MIXED, int APT, int MEM, int TPA, bool GB>
 cudaError_t run_t(const MinArgs* a, int n_clusters, int C, int threads, size_t smem,
                          cudaStream_t s, int* max_clusters) {
-  auto kern = k_minimize<D, MIXED, APT, MEM, TPA>;
+  auto kern = k_minimize<D, MIXED, APT, MEM, TPA, GB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if constexpr (GB) {
+    // cooperative launch of n_clusters replicas x C consecutive CTAs; every CTA
+    // must be resident (the launch fails otherwise, it never waits)
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (max_clusters) {
+      *max_clusters = per_sm * sm_count() / C;
+      return cudaSuccess;
+    }
+    if ((int64_t)n_clusters * C > (int64_t)per_sm * sm_count()) return cudaErrorCooperativeLaunchTooLarge;
+    MinArgs args = *a;
+    args.gb_C = C;
+    void* params[] = {&args};
+    count_launch();
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(n_clusters * C), dim3(threads),
+                                       params, smem, s);
+  }
   if (C > 8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
@@ -72,32 +90,37 @@ cudaError_t run_t(const MinArgs* a, int n_clusters, int C, int threads, size_t s
   return cudaLaunchKernelEx(&cfg, kern, *a);
 }
 
-template <int D, bool MIXED, int MEM, int TPA>
+template <int D, bool MIXED, int MEM, int TPA, bool GB>
 cudaError_t run_apt(const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
                            cudaStream_t s, int* max_clusters) {
   int apt, threads;
   choose_apt(D, npc, &apt, &threads, TPA);
   if (threads > ((minimize_is_lean(D, apt) || TPA > 1) ? 1024 : 512)) return cudaErrorInvalidValue;
   if constexpr (TPA > 1) {
-    return run_t<D, MIXED, 1, MEM, TPA>(a, n_clusters, C, threads, smem, s, max_clusters);
+    return run_t<D, MIXED, 1, MEM, TPA, GB>(a, n_clusters, C, threads, smem, s, max_clusters);
   } else {
     switch (apt) {
-      case 1: return run_t<D, MIXED, 1, MEM, 1>(a, n_clusters, C, threads, smem, s, max_clusters);
-      case 2: return run_t<D, MIXED, 2, MEM, 1>(a, n_clusters, C, threads, smem, s, max_clusters);
-      case 4: return run_t<D, MIXED, 4, MEM, 1>(a, n_clusters, C, threads, smem, s, max_clusters);
-      default: return run_t<D, MIXED, 8, MEM, 1>(a, n_clusters, C, threads, smem, s, max_clusters);
+      case 1: return run_t<D, MIXED, 1, MEM, 1, GB>(a, n_clusters, C, threads, smem, s, max_clusters);
+      case 2: return run_t<D, MIXED, 2, MEM, 1, GB>(a, n_clusters, C, threads, smem, s, max_clusters);
+      case 4: return run_t<D, MIXED, 4, MEM, 1, GB>(a, n_clusters, C, threads, smem, s, max_clusters);
+      default: return run_t<D, MIXED, 8, MEM, 1, GB>(a, n_clusters, C, threads, smem, s, max_clusters);
     }
   }
 }
 
-template <int D, bool MIXED, int TPA>
+template <int D, bool MIXED, int TPA, bool GB = false>
 cudaError_t run_mem(int mem, const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
                            cudaStream_t s, int* max_clusters) {
-  switch (mem) {
-    case 3: return run_apt<D, MIXED, 3, TPA>(a, n_clusters, C, npc, smem, s, max_clusters);
-    case 2: return run_apt<D, MIXED, 2, TPA>(a, n_clusters, C, npc, smem, s, max_clusters);
-    case 1: return run_apt<D, MIXED, 1, TPA>(a, n_clusters, C, npc, smem, s, max_clusters);
-    default: return run_apt<D, MIXED, 0, TPA>(a, n_clusters, C, npc, smem, s, max_clusters);
+  if constexpr (GB) {  // global neighbour records only
+    if (mem == 0) return run_apt<D, MIXED, 0, TPA, true>(a, n_clusters, C, npc, smem, s, max_clusters);
+    return run_apt<D, MIXED, 3, TPA, true>(a, n_clusters, C, npc, smem, s, max_clusters);
+  } else {
+    switch (mem) {
+      case 3: return run_apt<D, MIXED, 3, TPA, false>(a, n_clusters, C, npc, smem, s, max_clusters);
+      case 2: return run_apt<D, MIXED, 2, TPA, false>(a, n_clusters, C, npc, smem, s, max_clusters);
+      case 1: return run_apt<D, MIXED, 1, TPA, false>(a, n_clusters, C, npc, smem, s, max_clusters);
+      default: return run_apt<D, MIXED, 0, TPA, false>(a, n_clusters, C, npc, smem, s, max_clusters);
+    }
   }
 }
 
@@ -110,6 +133,15 @@ cudaError_t run_mem_3_fp64(int mem, const MinArgs* a, int n_clusters, int C, int
                            cudaStream_t s, int* max_clusters);
 cudaError_t run_mem_3_mixed(int mem, const MinArgs* a, int n_clusters, int C, int npc, size_t smem,
                             cudaStream_t s, int* max_clusters);
+// grid-barrier (cooperative) launches, one unit each
+cudaError_t run_mem_2_fp64_gb(int mem, const MinArgs* a, int n_clusters, int C, int npc,
+                              size_t smem, cudaStream_t s, int* max_clusters);
+cudaError_t run_mem_2_mixed_gb(int mem, const MinArgs* a, int n_clusters, int C, int npc,
+                               size_t smem, cudaStream_t s, int* max_clusters);
+cudaError_t run_mem_3_fp64_gb(int mem, const MinArgs* a, int n_clusters, int C, int npc,
+                              size_t smem, cudaStream_t s, int* max_clusters);
+cudaError_t run_mem_3_mixed_gb(int mem, const MinArgs* a, int n_clusters, int C, int npc,
+                               size_t smem, cudaStream_t s, int* max_clusters);
 // the split force phase (two threads per atom), one unit each
 cudaError_t run_mem_2_fp64_t2(int mem, const MinArgs* a, int n_clusters, int C, int npc,
                               size_t smem, cudaStream_t s, int* max_clusters);

@@ -79,12 +79,20 @@ struct aqs_system {
   bool tuning = false;
   struct Tuned {
     int C, staging, tpa;
+    bool gb;
   };
   std::map<std::pair<int, int64_t>, Tuned> tuned;
   // threads per atom of the force phase (1 or 2; the autotuner may choose 2
   // where 2 npc threads fit a CTA); tpa_user marks a caller's choice
   int tpa = 1;
   bool tpa_user = false;
+  // grid barriers (aqs_set_grid_barrier): the replicas' CTAs run in one
+  // cooperative launch without clusters and synchronise through global memory
+  bool grid_barrier = false;
+  bool grid_barrier_user = false;
+  double* gb_part = nullptr;
+  unsigned* gb_bar = nullptr;  // one 64-bit arrival counter per replica
+  int* gb_err = nullptr;
   // staging mode of the minimiser launches (-1: automatic); staging_user marks
   // a mode the caller fixed, which the tuner leaves alone
   int staging = -1;
@@ -170,6 +178,10 @@ void* dalloc(aqs_system* s, size_t bytes) {
     cudaGetLastError();
     p = nullptr;
   }
+  if (p && (reinterpret_cast<uintptr_t>(p) & 15u)) {  // the kernels need 16-byte alignment
+    if (s->ufree) s->ufree(p, s->actx);
+    return nullptr;
+  }
   if (p) s->allocs.push_back({p, bytes});
   return p;
 }
@@ -219,13 +231,15 @@ void cell_widths(int D, const double* H, double* w) {
 }
 
 // Cluster size for R concurrently minimised replicas of n atoms: the largest
-// C (at most 16, at least 32 atoms and at most 4096 atoms per CTA) at which
-// the device holds all R clusters at once (cudaOccupancyMaxActiveClusters;
+// C (at most 16 and SMs / R, at least 32 atoms and at most 4096 atoms per CTA)
+// at which the device holds all R clusters at once (cudaOccupancyMaxActiveClusters;
 // clusters are placed per GPC, so e.g. 23 clusters of 6 CTAs fit a GB300 but
 // only 15 of 7-9).  When no size holds all R, the size with the most resident
 // CTAs.
 int auto_cluster(int dim, bool mixed, int R, int64_t n, int nt, int cap) {
-  const int Cmax = (int)std::min<int64_t>(kMaxCluster, std::max<int64_t>(1, n / 32));
+  const int Cmax = (int)std::min<int64_t>(
+      std::min<int64_t>(kMaxCluster, std::max(1, sm_count() / std::max(1, R))),
+      std::max<int64_t>(1, n / 32));
   int fallback = 0, most = -1;
   for (int C = Cmax; C >= 1; C--) {
     const int64_t npc = (n + C - 1) / C;
@@ -241,6 +255,19 @@ int auto_cluster(int dim, bool mixed, int R, int64_t n, int nt, int cap) {
   int C = 1;
   while ((n + C - 1) / C > 4096 && C < kMaxCluster) C++;
   return C;
+}
+
+// Grid-barrier launches: the largest C (at most 16, at least 32 atoms and at
+// most 4096 atoms per CTA) at which R replicas' CTAs are all resident.
+int gb_cluster(int dim, bool mixed, int R, int64_t n, int nt, int cap, int staging) {
+  const int Cmax = (int)std::min<int64_t>(kMaxCluster, std::max<int64_t>(1, n / 32));
+  for (int C = Cmax; C >= 1; C--) {
+    const int64_t npc = (n + C - 1) / C;
+    if (npc > 4096) break;
+    if (minimize_max_grid_replicas(dim, mixed, C, (int)npc, (int)n, nt, cap, staging) >= R)
+      return C;
+  }
+  return 0;
 }
 
 aqs_status upload_geom(aqs_system* s) {
@@ -505,6 +532,10 @@ MinArgs min_args(aqs_system* s, const aqs_fire_params* f) {
   a.lean64 = s->lean64;
   a.hist = nullptr;
   a.hist_stride = 0;
+  a.gb_C = 0;
+  a.gb_part = nullptr;
+  a.gb_bar = nullptr;
+  a.gb_err = nullptr;
   for (int k = 0; k < AQS_MAX_TYPES * AQS_MAX_TYPES; k++) a.rl2f[k] = s->rl2f[k];
   return a;
 }
@@ -571,13 +602,37 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
       if (it == s->tuned.end()) {
         int best = 0, mode = -1;
         AQS_TRY(tune_clusters(s, f, mask, s->tune_iters, &best, &mode, nullptr, nullptr));
-        s->tuned[key] = aqs_system::Tuned{best, mode, s->tpa};
+        s->tuned[key] = aqs_system::Tuned{best, mode, s->tpa, s->grid_barrier};
       } else {
         if (!s->staging_user) s->staging = it->second.staging;
         if (!s->tpa_user) s->tpa = it->second.tpa;
+        if (!s->grid_barrier_user) s->grid_barrier = it->second.gb;
         AQS_TRY(apply_cluster(s, reps, it->second.C));
       }
     }
+  }
+  if (s->grid_barrier && s->C_override <= 0 && !s->tuning && s->tune_iters <= 0) {
+    // one cooperative launch holds every replica: one C for all of them
+    std::vector<int> reps;
+    int64_t nmax = 0;
+    for (int r = 0; r < s->R; r++)
+      if (jobs[r].nsteps > 0) {
+        reps.push_back(r);
+        nmax = std::max(nmax, s->n[r]);
+      }
+    if (!reps.empty()) {
+      const int C = gb_cluster(s->dim, s->prec == AQS_MIXED, (int)reps.size(), nmax, s->nt,
+                               s->cap, s->staging);
+      if (C <= 0) return fail(AQS_ERR_UNSUPPORTED, "grid barriers: the replicas do not fit the device");
+      AQS_TRY(apply_cluster(s, reps, C));
+    }
+  }
+  if (s->grid_barrier && !s->gb_part) {
+    AQS_TRY(alloc_arr(s, &s->gb_part, (size_t)s->R * kMaxCluster * kNumRed));
+    AQS_TRY(alloc_arr(s, &s->gb_bar, (size_t)2 * s->R));
+    AQS_TRY(alloc_arr(s, &s->gb_err, (size_t)1));
+    CUDA_TRY(cudaMemsetAsync(s->gb_bar, 0, sizeof(unsigned) * 2 * s->R, s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->gb_err, 0, sizeof(int), s->stream));
   }
   int64_t maxsteps = 0;
   bool snap = false;
@@ -657,6 +712,8 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
         if (s->geom[r].C == C) order_work.push_back(r);
       groups.push_back({start, (int)order_work.size() - start});
     }
+    if (s->grid_barrier && groups.size() > 1)
+      return fail(AQS_ERR_UNSUPPORTED, "grid barriers need one cluster size for all replicas");
     CUDA_TRY(cudaMemcpyAsync(s->d_work, order_work.data(), sizeof(int) * order_work.size(),
                              cudaMemcpyHostToDevice, s->stream));
     if (!s->lean32) {  // first lean launch of this system
@@ -669,6 +726,11 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
     }
     MinArgs a = min_args(s, f);
     a.warm_u = warm_u;
+    if (s->grid_barrier) {
+      a.gb_part = s->gb_part;
+      a.gb_bar = s->gb_bar;
+      a.gb_err = s->gb_err;
+    }
     if (s->hist_launch) {
       a.hist = s->d_hist;
       a.hist_stride = s->hist_cap;
@@ -699,14 +761,27 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
         st = s->aux[gi % 4];
         CUDA_TRY(cudaStreamWaitEvent(st, s->aux_ev[4], 0));
       }
+      if (s->grid_barrier)  // the barrier counters start at zero in every launch
+        CUDA_TRY(cudaMemsetAsync(s->gb_bar, 0, sizeof(unsigned) * 2 * s->R, st));
       CUDA_TRY(launch_minimize(s->dim, s->prec == AQS_MIXED, a, groups[gi].second, C, npc, nrep,
-                               s->cap, st, s->staging, s->tpa));
+                               s->cap, st, s->staging, s->tpa, s->grid_barrier));
       if (multi) CUDA_TRY(cudaEventRecord(s->aux_ev[gi % 4], st));
       if (multi && (gi % 4 == 3 || gi + 1 == groups.size()))
         for (size_t k = 0; k <= gi % 4; k++) CUDA_TRY(cudaStreamWaitEvent(s->stream, s->aux_ev[k], 0));
     }
     if (timing) CUDA_TRY(cudaEventRecord(s->ev1, s->stream));
     AQS_TRY(download_state(s));
+    if (s->grid_barrier) {
+      int err = 0;
+      CUDA_TRY(cudaMemcpy(&err, s->gb_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (err) {
+        // the barrier words may be left mid-barrier: clear them for the next call
+        CUDA_TRY(cudaMemsetAsync(s->gb_bar, 0, sizeof(unsigned) * 2 * s->R, s->stream));
+        CUDA_TRY(cudaMemsetAsync(s->gb_err, 0, sizeof(int), s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        return fail(AQS_ERR_TIMEOUT, "a grid-barrier wait ran out (CTAs not resident?)");
+      }
+    }
     if (timing) {
       float ms = 0.f;
       CUDA_TRY(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
@@ -742,9 +817,17 @@ aqs_status run_jobs(aqs_system* s, const aqs_fire_params* f, const std::vector<J
     // fewer replicas left: give each a larger cluster (the list is rebuilt
     // for the new owner layout; the FIRE state carries over)
     if (s->C_override <= 0 && !next.empty() && next.size() < todo.size()) {
+      int Cg = 0;
+      if (s->grid_barrier) {
+        int64_t nmax = 0;
+        for (int r : next) nmax = std::max(nmax, s->n[r]);
+        Cg = gb_cluster(s->dim, s->prec == AQS_MIXED, (int)next.size(), nmax, s->nt, s->cap,
+                        s->staging);
+      }
       for (int r : next) {
-        int Cn = auto_cluster(s->dim, s->prec == AQS_MIXED, (int)next.size(), s->n[r], s->nt,
-                              s->cap);
+        int Cn = s->grid_barrier ? Cg
+                                 : auto_cluster(s->dim, s->prec == AQS_MIXED, (int)next.size(),
+                                                s->n[r], s->nt, s->cap);
         if (Cn > s->geom[r].C) {
           s->geom[r].C = Cn;
           s->geom[r].npc = (int)((s->n[r] + Cn - 1) / Cn);
@@ -1041,6 +1124,8 @@ aqs_status ensure_chains(aqs_system* s, int src, int P) {
   c->staging_user = s->staging_user;
   c->tpa = s->tpa_user ? s->tpa : 1;
   c->tpa_user = s->tpa_user;
+  c->grid_barrier = s->grid_barrier_user ? s->grid_barrier : false;
+  c->grid_barrier_user = s->grid_barrier_user;
   s->chains = c;
   return AQS_OK;
 }
@@ -1841,7 +1926,7 @@ aqs_status aqs_autotune_clusters(aqs_system* s, const aqs_fire_params* f, int64_
       nmax = std::max(nmax, s->n[r]);
       cnt++;
     }
-  if (best > 0) s->tuned[std::make_pair(cnt, nmax)] = aqs_system::Tuned{best, mode, s->tpa};
+  if (best > 0) s->tuned[std::make_pair(cnt, nmax)] = aqs_system::Tuned{best, mode, s->tpa, s->grid_barrier};
   if (best_cluster) *best_cluster = best;
   if (best_staging) *best_staging = mode;
   return AQS_OK;
@@ -1868,6 +1953,26 @@ aqs_status aqs_set_threads_per_atom(aqs_system* s, int tpa) {
 }
 
 int aqs_threads_per_atom(const aqs_system* s) { return s ? s->tpa : 0; }
+
+aqs_status aqs_set_grid_barrier(aqs_system* s, int on) {
+  if (!s || on < -1 || on > 1) return fail(AQS_ERR_INVALID_ARG, "grid barrier: -1, 0 or 1");
+  s->grid_barrier = on == 1;
+  s->grid_barrier_user = on >= 0;
+  s->tuned.clear();
+  if (s->grid_barrier && s->tpa > 1) s->tpa = 1;
+  if (s->chains) {
+    s->chains->grid_barrier = s->grid_barrier;
+    s->chains->grid_barrier_user = s->grid_barrier_user;
+    s->chains->tuned.clear();
+  }
+  return AQS_OK;
+}
+
+int aqs_grid_barrier(const aqs_system* s, int of_chains) {
+  if (!s) return -1;
+  if (of_chains) return s->chains ? (s->chains->grid_barrier ? 1 : 0) : -1;
+  return s->grid_barrier ? 1 : 0;
+}
 
 int aqs_max_active_clusters(const aqs_system* s, int replica, int C, int staging, int tpa) {
   if (!s || replica < 0 || replica >= s->R || C < 1 || C > kMaxCluster) return -1;
@@ -2056,6 +2161,12 @@ bool cluster_feasible(const aqs_system* s, const std::vector<int>& reps, int C) 
   for (int r : reps) {
     const int64_t npc = (s->n[r] + C - 1) / C;
     if (npc > 4096 || (C > 1 && s->n[r] < 32 * (int64_t)C)) return false;
+    if (s->grid_barrier) {
+      if (minimize_max_grid_replicas(s->dim, s->prec == AQS_MIXED, C, (int)npc, (int)s->n[r],
+                                     s->nt, s->cap, s->staging) < (int)reps.size())
+        return false;
+      continue;
+    }
     if (minimize_max_active_clusters(s->dim, s->prec == AQS_MIXED, C, (int)npc, (int)s->n[r],
                                      s->nt, s->cap, s->staging, s->tpa) <= 0)
       return false;
@@ -2124,49 +2235,64 @@ aqs_status tune_clusters(aqs_system* s, const aqs_fire_params* f, const std::vec
   aqs_fire_params fw = ft;
   fw.max_iter = std::min<int64_t>(iters, 32);
   const int saved_override = s->C_override, saved_staging = s->staging, saved_tpa = s->tpa;
+  const bool saved_gb = s->grid_barrier;
   s->tuning = true;
   int bestC = 0, bestM = s->staging, bestTPA = s->tpa;
+  bool bestGB = s->grid_barrier;
   double bestT = 1e300;
-  // time per iteration of every candidate: [C][tpa - 1][mode]
-  std::vector<double> table((size_t)(kMaxCluster + 1) * 2 * kNumStaging, -1.0);
+  // time per iteration of every candidate: [barrier mode][C][tpa - 1][staging]
+  const size_t per_mode = (size_t)(kMaxCluster + 1) * 2 * kNumStaging;
+  std::vector<double> table(2 * per_mode, -1.0);
   aqs_status err = AQS_OK;
-  for (int C = 1; C <= kMaxCluster && err == AQS_OK; C++) {
-    const int npc = (int)((nmax + C - 1) / C);
-    // threads per atom of the force phase ("atoms per warp" 32 or 16), unless
-    // the caller fixed it
-    for (int tpa = 1; tpa <= 2 && err == AQS_OK; tpa++) {
-      if (s->tpa_user && tpa != saved_tpa) continue;
-      if (tpa == 2 && minimize_tpa(npc, 2) != 2) continue;
-      // every staging mode that fits: the mode decides the shared memory of
-      // a CTA and with it how many CTAs (of different clusters) share an SM,
-      // so it decides how many clusters are resident at once
-      for (int m = 0; m < kNumStaging && err == AQS_OK; m++) {
-        if (s->staging_user && m != saved_staging) continue;
-        if (minimize_staging(s->dim, npc, (int)nmax, s->nt, s->cap, m) != m) continue;
-        s->tpa = tpa;
-        s->staging = m;
-        if (!cluster_feasible(s, reps, C)) continue;
-        double ms = 0.0;
-        if ((err = time_candidate(s, ft, fw, mask, reps, tilt, C, &ms)) != AQS_OK) break;
-        table[((size_t)C * 2 + (tpa - 1)) * kNumStaging + m] = ms;
-        if (ms_per_iter && (ms_per_iter[C] < 0.0 || ms < ms_per_iter[C])) ms_per_iter[C] = ms;
-        if (ms < bestT) {
-          bestT = ms;
-          bestC = C;
-          bestTPA = tpa;
-          bestM = m;
+  // one barrier mode: every cluster size, threads per atom and staging mode
+  auto search = [&](bool gb) {
+    s->grid_barrier = gb;
+    for (int C = 1; C <= kMaxCluster && err == AQS_OK; C++) {
+      const int npc = (int)((nmax + C - 1) / C);
+      // threads per atom of the force phase ("atoms per warp" 32 or 16), unless
+      // the caller fixed it (grid barriers: one)
+      for (int tpa = 1; tpa <= 2 && err == AQS_OK; tpa++) {
+        if (s->tpa_user && tpa != saved_tpa) continue;
+        if (tpa == 2 && (gb || minimize_tpa(npc, 2) != 2)) continue;
+        // every staging mode that fits: the mode decides the shared memory of
+        // a CTA and with it how many CTAs (of different clusters) share an SM,
+        // so it decides how many clusters are resident at once
+        for (int m = 0; m < kNumStaging && err == AQS_OK; m++) {
+          if (s->staging_user && m != saved_staging) continue;
+          if (gb && m != 0 && m != 3) continue;
+          if (minimize_staging(s->dim, npc, (int)nmax, s->nt, s->cap, m) != m) continue;
+          s->tpa = tpa;
+          s->staging = m;
+          if (!cluster_feasible(s, reps, C)) continue;
+          double ms = 0.0;
+          if ((err = time_candidate(s, ft, fw, mask, reps, tilt, C, &ms)) != AQS_OK) break;
+          table[(gb ? per_mode : 0) + ((size_t)C * 2 + (tpa - 1)) * kNumStaging + m] = ms;
+          if (ms_per_iter && (ms_per_iter[C] < 0.0 || ms < ms_per_iter[C])) ms_per_iter[C] = ms;
+          if (ms < bestT) {
+            bestT = ms;
+            bestC = C;
+            bestTPA = tpa;
+            bestM = m;
+            bestGB = gb;
+          }
         }
       }
     }
-  }
+  };
+  // thread-block clusters, and (unless the caller fixed the mode) one
+  // cooperative launch with global-memory barriers
+  if (!s->grid_barrier_user || !saved_gb) search(false);
+  if (err == AQS_OK && (!s->grid_barrier_user || saved_gb)) search(true);
   if (ms_per_staging && bestC > 0)
     for (int m = 0; m < kNumStaging; m++)
-      ms_per_staging[m] = table[((size_t)bestC * 2 + (bestTPA - 1)) * kNumStaging + m];
+      ms_per_staging[m] =
+          table[(bestGB ? per_mode : 0) + ((size_t)bestC * 2 + (bestTPA - 1)) * kNumStaging + m];
   if (s->staging_user) bestM = saved_staging;
   s->tuning = false;
   s->C_override = saved_override;
   s->staging = err == AQS_OK ? bestM : saved_staging;
   s->tpa = err == AQS_OK ? bestTPA : saved_tpa;
+  s->grid_barrier = err == AQS_OK ? bestGB : saved_gb;
   for (int r : reps) {
     const int C = (err == AQS_OK && bestC > 0) ? bestC : c0[r];
     s->geom[r].C = C;

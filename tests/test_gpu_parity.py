@@ -270,6 +270,31 @@ def test_full_size_workload_properties(A, syn):
         assert np.sqrt((Fr * Fr).sum(1)).max() < 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_reduced_benchmark_shape_matches_golden(A, syn, prec):
+    """Algorithm 1 at the benchmark's shape, reduced to a size the oracle can
+    run: the N = 1024 glass, dgamma = 1e-4, P = 4 chains of K = 10, 400 steps
+    (gamma = 0.04), against the stored oracle run (11 passes, 2 rejections, 5
+    plastic events): the decision log, energies, events and the final
+    configuration."""
+    g = load_golden("glass_2d_n1024_s0.npz")
+    gold = load_golden("par_2d_n1024_s0.npz")
+    P = A.AQS_FP64 if prec == "fp64" else A.AQS_MIXED
+    s = make_system(A, syn, g["x"], g["types"], g["H"], P)
+    r = s.parallel_step(float(gold["dgamma"]), int(gold["K"]), int(gold["P"]),
+                        int(gold["n_steps"]), eq_tol=float(gold["eq_tol"]))
+    assert r["iterations"] == int(gold["iterations"])
+    assert np.array_equal(r["log_i"], gold["log_i"])
+    assert np.array_equal(r["log_eq"], gold["log_eq"])
+    rel = 1e-9 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(r["E"], gold["E"], rtol=rel)
+    np.testing.assert_allclose(r["tau"], gold["tau"], rtol=1e-6, atol=1e-7)
+    assert np.array_equal(r["D"] > EV_THR, gold["D"] > EV_THR)
+    assert mi_disp(s.positions(), gold["x"], gold["H"]) < 1e-6
+    np.testing.assert_allclose(s.box(), gold["H"], rtol=1e-12)
+    s.close()
+
+
 def test_benchmark_pass_spot_checked_by_the_oracle(A, orc, syn):
     """One pass of the benchmark's Algorithm 1 (N = 4096 glass, P = 16,
     K = 10, dgamma = 1e-4, mixed precision, autotuned launch) against plain
