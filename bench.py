@@ -74,10 +74,10 @@ FLOP64_PER_PAIR = 32
 #   the chains (thread-block clusters, or one cooperative launch with grid
 #   barriers); the kernel runs from L2, and its DRAM traffic is the working
 #   set read once per launch
-TRAFFIC_CFG1_PER_LAUNCH = {"cluster": 10_614_016, "grid_barrier": None}
+TRAFFIC_CFG1_PER_LAUNCH = {"cluster": 10_614_016, "grid_barrier": 11_797_504}
 #   3D (N = 65536), per replica-iteration of the timed launch (6 replicas x
-#   200 iterations: 36.16 GB read + 0.52 GB written)
-TRAFFIC_3D_PER_REPLICA_ITER = 30_570_000
+#   200 iterations: 36.10 GB read + 0.46 GB written)
+TRAFFIC_3D_PER_REPLICA_ITER = 30_465_000
 
 CONFIG = {"workload": "2D binary LJ glass (65:35, rho=1.2), N=4096, Algorithm 1 with P=16 "
                       "chains of K=10 fine steps, dgamma=1e-4, FIRE to |F|max<1e-10, mixed "
@@ -435,6 +435,107 @@ def run_warm(args):
            "detail": {"train_step_ms": 1e3 * t_train, "train_rows_per_s": batch / t_train,
                       "train_tflops": train_tf, "train_frac": train_tf / peak,
                       "features_ms": 1e3 * t_feat, "features_rows_per_s": rows / t_feat}})
+
+
+def run_warm_eval(args):
+    """The learned warm start at the scale of its workload.  Training data come
+    from the method itself: 16 N = 4096 glasses (seeds 100..115, mixed-
+    precision GPU quench), `warm_collect` over 4 AQS steps of dgamma = 1e-4
+    (features of each minimum, the non-affine displacement per unit strain of
+    the next step as target): 262 144 per-atom rows, the last step held out.
+    Evaluation on 8 held-out glasses of N = 16384 (seeds 0..7, one batched
+    system): `steps` sequential AQS steps with the gated learned start against
+    the plain affine start from the same minima (Algorithm 1 does not take the
+    learned start).  value = FIRE iterations of the plain run / those of the
+    learned run (above 1: the learned start saves iterations); the detail
+    gives both runs' iterations per step and steps/s (device time), the steps
+    that kept the learned start, and how far the two runs' energies and event
+    steps agree."""
+    import torch
+    from paper_2507_20802_gb300 import aqs as A, synthetic as syn
+    torch.cuda.set_device(0)
+    dg = 1e-4
+
+    def glasses(n, seeds):
+        xs, ts, Hs = [], [], []
+        for sd in seeds:
+            x, t, H = syn.random_glass_start(n, 2, seed=sd)
+            xs.append(x); ts.append(t); Hs.append(H)
+        g = A.System(np.concatenate(xs), np.concatenate(ts), np.stack(Hs), [n] * len(seeds),
+                     syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR, precision=A.AQS_MIXED)
+        q = g.minimize(A.fire_params(max_iter=args.quench_iters))
+        assert all(r["status"] == 0 for r in q), [r["status"] for r in q]
+        return g, np.concatenate(ts), max(r["iters"] for r in q)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        e1.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    l0 = A.aqs_launch_count()
+    # ---- training data: 16 x 4096 atoms, 4 steps
+    n_tr, g_tr, st_tr = 4096, 16, 4
+    tr, _, q_tr = glasses(n_tr, range(100, 100 + g_tr))
+    rows_step = n_tr * g_tr
+    F = torch.zeros((st_tr * rows_step, A.WARM_IN), dtype=torch.bfloat16, device="cuda")
+    T = torch.zeros((st_tr * rows_step, 2), dtype=torch.float32, device="cuda")
+    _, t_collect = timed(lambda: tr.warm_collect(dg, st_tr, F, T))
+    tr.close()
+    n_train = (st_tr - 1) * rows_step
+    w = A.Warm(seed=1)
+    batch, iters = 65536, args.warm_train_iters
+    losses = []
+
+    def train():
+        for it in range(iters):
+            i = it % (n_train // batch)
+            lr = 2e-3 if it < (2 * iters) // 3 else 5e-4
+            losses.append(w.train_step(F[i * batch:(i + 1) * batch], T[i * batch:(i + 1) * batch],
+                                       lr))
+    _, t_train = timed(train)
+    held, _ = w.loss_grad(F[n_train:], T[n_train:])
+    base = 0.5 * float((T[n_train:] ** 2).sum(dim=1).mean())
+    del F, T
+    # ---- evaluation: 8 held-out glasses of 16384 atoms
+    n_ev, g_ev = 16384, 8
+    plain, t_ev, q_ev = glasses(n_ev, range(g_ev))
+    x0 = np.concatenate([plain.positions(r) for r in range(g_ev)])
+    H0 = np.stack([plain.box(r) for r in range(g_ev)])
+    warm = A.System(x0, t_ev, H0, [n_ev] * g_ev, syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR,
+                    precision=A.AQS_MIXED)
+    steps = max(1, args.steps)
+    with Clocks(0) as clk:
+        rp, t_plain = timed(lambda: plain.run_sequential(dg, steps))
+        rw, t_warm = timed(lambda: warm.run_sequential_warm(w, dg, steps))
+    it_p, it_w = int(rp["iters"].sum()), int(rw["iters"].sum())
+    e_dev = float(np.max(np.abs(rw["E"] - rp["E"]) / np.abs(rp["E"])))
+    ev_same = bool(np.array_equal(rw["D"] > 1e-2, rp["D"] > 1e-2))
+    config = {"workload": "learned warm start: MLP trained on 4 AQS steps of 16 N=4096 2D glasses "
+                          "(seeds 100-115, 262144 rows, last step held out); sequential AQS "
+                          "dgamma=1e-4 on 8 held-out N=16384 glasses (seeds 0-7), gated learned "
+                          "start vs plain affine start, mixed precision",
+              "train_glasses": g_tr, "train_atoms": n_tr, "train_rows": n_train,
+              "eval_glasses": g_ev, "eval_atoms": n_ev, "steps": steps, "dgamma": dg,
+              "l2": "working set on chip / L2; not flushed"}
+    _line("FIRE-iteration gain of the learned warm start (plain / learned)", it_p / max(1, it_w),
+          "x", args, 1e3 * (t_plain + t_warm), config,
+          {"gpu_launches": A.aqs_launch_count() - l0, "clocks": clk.summary(),
+           "detail": {"fire_iters_per_glass_step_plain": it_p / (steps * g_ev),
+                      "fire_iters_per_glass_step_learned": it_w / (steps * g_ev),
+                      "glass_steps_per_s_plain": steps * g_ev / t_plain,
+                      "glass_steps_per_s_learned": steps * g_ev / t_warm,
+                      "learned_start_kept": int(rw["used"].sum()), "glass_steps": steps * g_ev,
+                      "max_rel_energy_diff": e_dev, "same_event_steps": ev_same,
+                      "train_loss_first_last": [losses[0], losses[-1]], "train_iters": iters,
+                      "held_out_loss": held, "zero_prediction_loss": base,
+                      "collect_s": t_collect, "train_s": t_train,
+                      "quench_iters_max": {"train": q_tr, "eval": q_ev}}})
+    plain.close()
+    warm.close()
 
 
 def _peaks():
@@ -851,7 +952,7 @@ def main():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--baseline-steps", type=int, default=20)
     ap.add_argument("--workload", choices=["cfg1", "batch64", "glass3d", "cfg3", "warm",
-                                           "oracle-threads", "sweep", "tune-table"],
+                                           "warm-eval", "oracle-threads", "sweep", "tune-table"],
                     default="cfg1")
     ap.add_argument("--tune-iters", type=int, default=500)
     ap.add_argument("--sweep-seeds", type=int, default=4)
@@ -874,6 +975,7 @@ def main():
                     help="FIRE iterations per autotuner candidate (0: size rule only)")
     ap.add_argument("--quench-iters", type=int, default=400000)
     ap.add_argument("--iters3d", type=int, default=2000)
+    ap.add_argument("--warm-train-iters", type=int, default=600)
     ap.add_argument("--replicas3d", type=int, default=32)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -884,6 +986,8 @@ def main():
         return run_batch64(args) or 0
     if args.workload == "warm":
         return run_warm(args) or 0
+    if args.workload == "warm-eval":
+        return run_warm_eval(args) or 0
     if args.workload == "glass3d":
         return run_glass3d(args) or 0
     if args.workload == "oracle-threads":
