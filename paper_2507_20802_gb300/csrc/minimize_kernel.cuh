@@ -253,8 +253,12 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Pub<D>* pub = reinterpret_cast<Pub<D>*>(smem_raw);  // MEM 2: whole replica, else own atoms
-  Pub<D>* mine = MEM == 2 ? pub + lo : pub;
-  const int pub_len = MEM == 2 ? A.nrep_launch : lstride;
+  // Mode 0 keeps the records of the CTA's own atoms in the global record
+  // array only: the shared memory they would take is left to L1, which holds
+  // the gathered neighbour records while the lists stream past.
+  constexpr bool OWN_G = MEM == 0;
+  Pub<D>* mine = MEM == 2 ? pub + lo : (OWN_G ? pubg + base : pub);
+  const int pub_len = MEM == 2 ? A.nrep_launch : (OWN_G ? 0 : lstride);
   double* sred = reinterpret_cast<double*>(smem_raw + sizeof(Pub<D>) * pub_len);  // [kNumRed]
   // this CTA's reduction partials: shared memory (read by the other CTAs of
   // the cluster through DSMEM), or a global slot per (replica, rank) with GB
@@ -422,7 +426,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
       dq[c] = Dl(k, c);
     }
     store_pub32<D>(&mine[li], qq, dq);
-    if (GREC) store_pub32<D>(&pubg[base + li], qq, dq);
+    if (GREC && !OWN_G) store_pub32<D>(&pubg[base + li], qq, dq);
   };
 #pragma unroll
   for (int k = 0; k < APT; k++) {
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__((minimize_is_lean(D, APT) || TPA > 1) ? 1024 :
     cell_origin<D>(H, g.nc, A.cell[gi], o);
     double* q = mine[li].q64;
     for (int c = 0; c < D; c++) q[c] = A.x[c * N + gi] - o[c];
-    if (GREC)
+    if (GREC && !OWN_G)
       for (int c = 0; c < D; c++) pubg[gi].q64[c] = q[c];
   };
   // record of a neighbour (owner CTA, slot) for the force phase

@@ -12,7 +12,9 @@ inline size_t smem_fixed(int nt) {
 inline size_t pub_size(int dim) { return dim == 2 ? sizeof(Pub<2>) : sizeof(Pub<3>); }
 
 inline size_t minimize_smem_bytes_impl(int dim, int npc, int nrep, int nt, int cap, int mem) {
-  size_t pub = pub_size(dim) * (size_t)(mem == 2 ? nrep : npc);
+  // records: the whole replica (mode 2), the CTA's own atoms (modes 1, 3), or
+  // none (mode 0 keeps them in the global record array)
+  size_t pub = pub_size(dim) * (size_t)(mem == 2 ? nrep : (mem == 0 ? 0 : npc));
   return pub + smem_fixed(nt) + (mem >= 1 ? sizeof(uint32_t) * (size_t)cap * npc : 0);
 }
 
@@ -51,6 +53,11 @@ cudaError_t run_t(const MinArgs* a, int n_clusters, int C, int threads, size_t s
   auto kern = k_minimize<D, MIXED, APT, MEM, TPA, GB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if constexpr (MEM == 0) {  // little shared memory: leave the rest of the SM's array to L1
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxL1);
+    if (e != cudaSuccess) return e;
+  }
   if constexpr (GB) {
     // cooperative launch of n_clusters replicas x C consecutive CTAs; every CTA
     // must be resident (the launch fails otherwise, it never waits)
