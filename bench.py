@@ -75,11 +75,10 @@ FLOP64_PER_PAIR = 32
 #   barriers); the kernel runs from L2, and its DRAM traffic is the working
 #   set read once per launch
 TRAFFIC_CFG1_PER_LAUNCH = {"cluster": 10_614_016, "grid_barrier": 11_797_504}
-#   3D (N = 65536), per replica-iteration of the timed launch: 30.5 MB (6
-#   replicas x 200 iterations: 36.10 GB read + 0.46 GB written) on the kernel
-#   that still kept its own records in shared memory in mode 0; not captured
-#   on the current mode-0 kernel
-TRAFFIC_3D_PER_REPLICA_ITER = None
+#   3D (N = 65536), per replica-iteration of the timed launch (6 replicas x
+#   200 iterations: 35.88 GB read + 0.45 GB written; a one-pass capture of the
+#   two DRAM counters)
+TRAFFIC_3D_PER_REPLICA_ITER = 30_277_000
 
 CONFIG = {"workload": "2D binary LJ glass (65:35, rho=1.2), N=4096, Algorithm 1 with P=16 "
                       "chains of K=10 fine steps, dgamma=1e-4, FIRE to |F|max<1e-10, mixed "

@@ -32,6 +32,7 @@ def make(A, syn, g, prec, R=1, **kw):
     s = A.System(np.tile(x, (R, 1)), np.tile(t, R), np.tile(H[None], (R, 1, 1)), [len(x)] * R,
                  syn.LJ_SIGMA, syn.LJ_EPS, syn.RC_FACTOR, precision=prec, **kw)
     s.set_grid_barrier(True)
+    assert s.grid_barrier() == 1 and s.grid_barrier(chains=True) == -1  # no chains yet
     return s
 
 
@@ -59,6 +60,7 @@ def test_grid_barrier_parallel_stepping_matches_golden(A, syn, prec):
     s = make(A, syn, g, P)
     r = s.parallel_step(float(gold["dgamma"]), int(gold["K"]), int(gold["P"]),
                         int(gold["n_steps"]), eq_tol=float(gold["eq_tol"]))
+    assert s.grid_barrier(chains=True) == 1  # the chains inherit the fixed mode
     assert np.array_equal(r["log_eq"], gold["log_eq"])
     assert np.array_equal(r["log_i"], gold["log_i"])
     rel = 1e-9 if prec == "fp64" else 1e-6
