@@ -76,7 +76,7 @@ FLOP64_PER_PAIR = 32
 #   set read once per launch
 TRAFFIC_CFG1_PER_LAUNCH = {"cluster": 10_614_016, "grid_barrier": 11_797_504}
 #   3D (N = 65536), per replica-iteration of the timed launch (6 replicas x
-#   200 iterations: 35.88 GB read + 0.45 GB written; a one-pass capture of the
+#   200 iterations: 35.88 GB read + 0.45 GB written; a capture of only the
 #   two DRAM counters)
 TRAFFIC_3D_PER_REPLICA_ITER = 30_277_000
 
